@@ -1,0 +1,317 @@
+"""Throughput of the Monte Carlo line-transfer pass on the 64^3, tau0 = 1e6
+uniform sphere (T = 1e4 K, a = 4.7e-4, central point source at line centre,
+FP32 walk, 400-bin escaped spectrum and per-cell scattering map).
+
+One step = one krl_run_packets launch over the next PACKETS_PER_STEP packet
+ids of the 1e6-packet job (every step of the pass runs: emission, cell walk,
+scattering, tallies, escape, regeneration, counter reduction). Inputs are
+resident on the device; L2 is flushed (a 256 MiB write) before every timed
+step and the step itself is bracketed by CUDA events on the launch stream.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PACKETS_PER_STEP = 1 << 18
+JOB_PACKETS = 1_000_000
+METRIC = "scatterings/s & packets/s (64³ τ0=1e6 sphere)"
+UNIT = "scatterings/s"
+# Algorithmic lane operations per event (derivation in the design doc): a
+# scattering = 2 Philox4x32-10 blocks + sampler inversion + Box-Muller +
+# isotropic direction + R_IIA frequency update + one segment; a face crossing
+# = profile lookup + exit distances + cell step.
+OPS_PER_SCAT = 330
+OPS_PER_CROSS = 50
+FP32_LANES_PER_SM = 128
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "transport_sphere64_tau1e6.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2608_09340_gb300", "csrc", "transport.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="krl", choices=["krl", "reference"])
+    ap.add_argument("--packets", type=int, default=PACKETS_PER_STEP)
+    ap.add_argument("--tau0", type=float, default=1e6,
+                    help="centre-to-edge line-centre depth (1e6 is the benchmark; smaller for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch recorded by the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+        src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        vals = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith(" "))
+        if vals.get("kernel_source_sha256_16", "").strip() != src_hash:
+            return None
+        return float(vals["dram_bytes_per_launch_scaled"].strip())
+    except Exception:
+        return None
+
+
+def run_reference(args, rank):
+    """The FP64 oracle as it stands, on the host cores, a bounded sample per step."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import workloads as W
+    p = W.sphere(vmax_kms=0.0)
+    cores = os.cpu_count() or 1
+    per_step = max(cores, 16)
+    oracle.build()
+    oracle.line_tables(float(p.line.a_fixed), False)
+    for s in range(args.warmup):
+        oracle.run(p, n=cores, first=s * per_step, nthreads=cores)
+    tot_scat = tot_pk = 0
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r = oracle.run(p, n=per_step, first=(args.warmup + s) * per_step, nthreads=cores)
+        tot_scat += int(r["stats"][4])
+        tot_pk += per_step
+    dt = time.perf_counter() - t0
+    val = tot_scat / dt
+    sample = f"{per_step} packets per step of the 64^3 tau0=1e6 static sphere (ids advance per step), FP64"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "packets_per_s": tot_pk / dt,
+        "config": {"workload": "sphere64_tau1e6_static", "packets_per_step": per_step},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(p):
+    """Oracle on a bounded sample (about 10 s of host work) at N = 1, rank 0."""
+    import oracle
+    cores = os.cpu_count() or 1
+    n = 4 * cores
+    oracle.line_tables(float(p.line.a_fixed), False)
+    t0 = time.perf_counter()
+    r = oracle.run(p, n=n, first=JOB_PACKETS - n, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": float(r["stats"][4]) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} packets (ids {JOB_PACKETS - n}..{JOB_PACKETS - 1}) of the same static sphere, "
+                      f"{int(r['stats'][4])} scatterings in {dt:.1f} s, FP64"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    import paper_2608_09340_gb300 as krl
+    from paper_2608_09340_gb300 import shard
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    krl.load_library()
+    dev = torch.device("cuda", local)
+    p = W.sphere(vmax_kms=0.0, tau0=args.tau0)
+    B = args.packets
+    g = krl.Grid(p, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    step_id = 0
+    for _ in range(args.warmup):
+        lo, n = shard.step_range(step_id, rank, world, B)
+        g.run(n=n, first=lo, want_stats=False)
+        step_id += 1
+    g.reset()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        lo, n = shard.step_range(step_id, rank, world, B)
+        ev[k][0].record(stream)
+        g.run(n=n, first=lo, want_stats=False)
+        ev[k][1].record(stream)
+        step_id += 1
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    kern_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    stats = g.tally("stats").cpu().numpy()
+    scat, cross, emitted = int(stats[4]), int(stats[5]), int(stats[0])
+    t_max = shard.max_over_ranks(kern_s)
+    tot = torch.tensor([scat, cross, emitted], dtype=torch.float64, device=dev)
+    shard.sum_over_ranks(tot)
+    scat_all, cross_all, pk_all = [float(v) for v in tot.cpu()]
+    value = scat_all / t_max
+
+    # roofline (ALU-bound walk): algorithmic lane-ops per launch / mean launch time
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+    ops = OPS_PER_SCAT * scat + OPS_PER_CROSS * cross
+    achieved = ops / kern_s
+    traffic = traffic_from_profile()
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak_ops, "traffic": traffic,
+            "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                           f"{sm_max:.0f} MHz ({peak_kind} max SM clock)",
+            "ops_per_scattering": OPS_PER_SCAT, "ops_per_crossing": OPS_PER_CROSS}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        op_host = torch.from_numpy(np.ascontiguousarray(p.opacity, dtype=np.float32)).pin_memory()
+        spec_h = torch.empty(p.spectrum[2] + 2, dtype=torch.float64).pin_memory()
+        scat_h = torch.empty(p.ncell, dtype=torch.int64).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        e_scat = 0
+        for k in range(args.steps):
+            q = W.sphere(vmax_kms=0.0, tau0=args.tau0)
+            q.opacity = op_host          # host buffer: copied by the binding's marshalling
+            gg = krl.Grid(q, device=dev)
+            lo, n = shard.step_range(step_id, rank, world, B)
+            st, _, _ = gg.run(n=n, first=lo, want_stats=True)
+            e_scat += st.scatterings
+            spec_h.copy_(gg.tally("spec_w"))
+            scat_h.copy_(gg.tally("scatmap"))
+            gg.close()
+            step_id += 1
+        torch.cuda.synchronize(dev)
+        e_dt = shard.max_over_ranks(time.perf_counter() - t0)
+        et = torch.tensor([float(e_scat)], dtype=torch.float64, device=dev)
+        shard.sum_over_ranks(et)
+        e2e = {"value": float(et.item()) / e_dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(op_host.numel() * 4),
+               "d2h_bytes_per_step": int(spec_h.numel() * 8 + scat_h.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(p)
+    g.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "packets_per_s": pk_all / t_max,
+            "config": {"workload": "sphere64_tau1e6_static" if args.tau0 == 1e6 else f"sphere64_tau{args.tau0:g}_static",
+                       "grid": "64^3", "tau0": args.tau0, "a": 4.7e-4,
+                       "T_K": 1e4, "source": "central point, line centre", "packets_per_step": B,
+                       "job_packets": JOB_PACKETS, "scatterings_per_packet": scat_all / max(pk_all, 1),
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"packet-id shards x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": 2 * args.steps, "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * krl.h - C ABI of the GB300 Monte Carlo line-transfer library (libkrl.so).
+ *
+ * The library implements the Monte Carlo photon-packet pass of the
+ * Kratos-linerad method (arXiv 2608.09340, Sec. 2): per-packet random walks
+ * through a 3-D Cartesian grid with optical-depth integration against a
+ * Voigt profile in the comoving frame (Sec. 2.1, Eq. xdef, Eq. sigma0),
+ * angle-dependent partial redistribution sampled from tables (Sec. 2.1.1,
+ * 2.1.2, Eq. riia-scatter), and tallies of the escaped spectrum, the
+ * excitation rate (Sec. 2.1.3), the velocity-resolved mean intensity and the
+ * camera-directed scattering emissivity (Sec. 2.2.1, Eq. scat-line).
+ *
+ * Conventions shared by every call:
+ *  - Pointers documented as "device" are CUDA device pointers (for example
+ *    torch.Tensor.data_ptr()); "host" pointers are ordinary CPU memory.
+ *  - Caller buffers are BORROWED for the duration of the call only; the
+ *    library copies what it keeps. The library owns everything it allocates
+ *    and frees it in krl_grid_destroy.
+ *  - Every call is ordered on the caller's stream `s` (a cudaStream_t; NULL
+ *    is the legacy default stream). A call synchronises `s` only when it
+ *    returns host data (documented per call).
+ *  - Every call returns a krl_status; on failure krl_last_error() returns a
+ *    thread-local message. No C++ exception crosses this boundary.
+ *  - Frequencies are in Doppler units x = (nu - nu0) / nu_D, positive to the
+ *    blue; a velocity v along the line of sight (receding positive) maps to
+ *    x = -v / b. Lengths inside the library are in cell widths.
+ *  - Grid fields are float32, C order [nz][ny][nx] (x fastest).
+ */
+#ifndef KRL_H
+#define KRL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KRL_API __attribute__((visibility("default")))
+#else
+#define KRL_API
+#endif
+
+typedef struct CUstream_st* krl_stream;
+
+typedef enum {
+    KRL_OK = 0,
+    KRL_ERR_ARG = -1,      /* invalid argument; nothing was enqueued            */
+    KRL_ERR_CUDA = -2,     /* a CUDA runtime call failed                         */
+    KRL_ERR_OOM = -3,      /* device allocation failed                           */
+    KRL_ERR_BUDGET = -4,   /* some packets hit the per-packet iteration budget   */
+    KRL_ERR_STATE = -5,    /* call out of order (e.g. run before krl_line_set)   */
+    KRL_ERR_NUMERIC = -6   /* NaN / negative field value, or a device numeric fault */
+} krl_status;
+
+/* Thread-local description of the last failure on this thread. */
+KRL_API const char* krl_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+KRL_API int krl_version(void);
+
+/* ------------------------------------------------------------------ grid */
+
+enum { KRL_PERIODIC_X = 1u, KRL_PERIODIC_Y = 2u, KRL_PERIODIC_Z = 4u };
+
+/* How `opacity` is given. */
+enum {
+    KRL_OPACITY_TAU = 0,   /* line-centre optical depth per cell width, n_l sigma0 dx */
+    KRL_OPACITY_NL = 1     /* lower-level number density n_l [cm^-3] (Eq. sigma0)     */
+};
+
+typedef struct {
+    int nx, ny, nz;             /* cells per axis, each >= 1; nx*ny*nz < 2^31     */
+    double cell_cm;             /* cubic cell width [cm], > 0                      */
+    uint32_t boundary_flags;    /* KRL_PERIODIC_*; other faces are open (escape)   */
+    int opacity_kind;           /* KRL_OPACITY_TAU or KRL_OPACITY_NL               */
+    const float* opacity;       /* device [nz][ny][nx], >= 0, required             */
+    double T_K;                 /* gas temperature [K], uniform (a single b and a
+                                   per line, the ph_mode 2 setting of Sec. 2.2.1)  */
+    const float* vx;            /* device [nz][ny][nx] bulk velocity [cm/s] or NULL */
+    const float* vy;
+    const float* vz;
+    const float* n_coll;        /* device collider density [cm^-3] or NULL (Eq. eps) */
+} krl_grid_desc;
+
+typedef struct krl_grid krl_grid;
+
+/*
+ * Create a grid: validates the fields (KRL_ERR_NUMERIC on NaN, Inf or a
+ * negative opacity / density) and copies them into library-owned device
+ * memory. Synchronises `s` (for the validation result). The fields are
+ * borrowed for this call only.
+ */
+KRL_API krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* desc, krl_stream s);
+
+/* Free everything the grid owns. Synchronises the device. NULL is a no-op. */
+KRL_API krl_status krl_grid_destroy(krl_grid* g);
+
+/* ------------------------------------------------------------------ line */
+
+enum { KRL_SRC_POINT = 0, KRL_SRC_PLANE = 1, KRL_SRC_BEAM = 2, KRL_SRC_VOLUME = 3 };
+enum { KRL_PROFILE_LINE_CENTRE = 0, KRL_PROFILE_GAUSSIAN = 1 };
+enum { KRL_TALLY_SCATMAP = 1u, KRL_TALLY_EXC = 2u, KRL_TALLY_J = 4u, KRL_TALLY_EMISS = 8u };
+#define KRL_MAX_CAMERAS 8
+
+typedef struct {
+    /* two-level line (Sec. 2.1) */
+    double nu0_hz;              /* rest frequency                                   */
+    double mass_amu;            /* mass of the absorber                             */
+    double A_ul;                /* Einstein A [s^-1]                                */
+    double g_u, g_l;            /* degeneracies                                     */
+    double k_ul;                /* collisional de-excitation coefficient [cm^3/s];
+                                   with the grid's n_coll gives epsilon (Eq. eps)  */
+    double a_fixed;             /* > 0: damping parameter; else A_ul/(4 pi nu_D)    */
+    /* photon source (Sec. 3) */
+    int src_kind;               /* KRL_SRC_*                                        */
+    double src_pos[3];          /* POINT: position (x, y, z) in cell units           */
+    int src_axis;               /* PLANE: normal axis; BEAM: travel axis (+ sense)  */
+    double src_plane;           /* PLANE: coordinate along src_axis, cell units      */
+    int band_axis;              /* BEAM: transverse axis with a limited entry band,
+                                   -1 for the whole face                            */
+    double band_lo, band_hi;    /* BEAM: band [lo, hi) in cell units                 */
+    int src_profile;            /* KRL_PROFILE_LINE_CENTRE or KRL_PROFILE_GAUSSIAN
+                                   (thermal profile exp(-x^2)/sqrt(pi))            */
+    const float* src_rate;      /* VOLUME: device per-cell emission weight (>= 0)   */
+    double luminosity;          /* photons per second of the whole run (scales
+                                   physical outputs; raw tallies use unit weight)  */
+    /* escaped spectrum (lab frame, all directions) */
+    double spec_xmin, spec_xmax;
+    int spec_nbins;             /* >= 1; bins half-open, plus under/overflow        */
+    /* velocity channels v_k = v_min + (k + 1/2) dv (Sec. 2.2.1) */
+    double ch_vmin_cms, ch_dv_cms;
+    int n_ch;                   /* 0 when neither J nor the emissivity is tallied   */
+    /* cameras: unit propagation direction toward the camera
+       (sin t cos p, sin t sin p, cos t) */
+    int n_cam;
+    double cam_theta[KRL_MAX_CAMERAS], cam_phi[KRL_MAX_CAMERAS];
+    uint32_t tally_flags;       /* KRL_TALLY_*                                      */
+} krl_line_desc;
+
+/*
+ * Attach a line to the grid: derives b = (2kT/m)^{1/2}, nu_D, a, sigma0
+ * (Eq. sigma0) and epsilon (Eq. eps); builds, in FP64 on the device, the
+ * ph_mode 2 Voigt slice at this a (5000 nodes in log10|x| on [-4, 3]), the
+ * velocity sampler (40 x-nodes x 251 u-nodes, log CDF) and the R_IIA table
+ * (Eq. riia-table, 201 Delta x 200 |x| x 40 g) and stores them as float32;
+ * derives the per-cell record {alpha0 dx, V/b}; allocates and zeroes the
+ * tallies. Replaces any previous line. Enqueued on `s`, which it
+ * synchronises once at the end (to read H(a,0) and the source-rate check:
+ * KRL_ERR_NUMERIC for a NaN/negative rate, KRL_ERR_ARG for a zero total).
+ */
+KRL_API krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream s);
+
+typedef struct {
+    double b_cms, nu_D_hz, a, sigma0_cm2, H0;  /* H0 = H(a, 0) as stored */
+    int ncell;
+} krl_line_info;
+
+/* Derived line constants (host). */
+KRL_API krl_status krl_line_info_get(const krl_grid* g, krl_line_info* out);
+
+/* ------------------------------------------------------------------ packets */
+
+enum { KRL_PREC_FP32 = 0, KRL_PREC_FP64 = 1 };
+
+/* Launch tuning; pass NULL for the defaults. Zero fields take the default. */
+typedef struct {
+    int precision;              /* KRL_PREC_FP32 (production) or KRL_PREC_FP64
+                                   (same walk in double, for lockstep checks)       */
+    int block;                  /* threads per CTA (multiple of 32, <= 1024)        */
+    int ctas_per_sm;            /* resident CTAs per SM of the persistent grid      */
+    int refill_min;             /* a warp takes new packets once at least this many
+                                   of its lanes are idle (1..32)                    */
+    uint64_t max_iters;         /* per-packet cap on walk iterations (budget)       */
+} krl_tune;
+
+/* One record per packet of a run (optional output). */
+typedef struct {
+    float x;                    /* lab-frame x at escape / destruction             */
+    uint32_t nscat;             /* scatterings                                     */
+    uint32_t ncross;            /* cell-face crossings                             */
+    uint16_t status;            /* 1 escaped, 2 destroyed, 3 budget exhausted       */
+    uint16_t pad;
+    uint32_t cell0;             /* flat index of the emission cell                 */
+} krl_packet_record;
+
+typedef struct {
+    uint64_t emitted, escaped, destroyed, stuck, scatterings, crossings;
+} krl_run_stats;
+
+/*
+ * Run packets with ids [first_id, first_id + n) under key `seed`
+ * (Philox4x32-10, counter = (id, event, block)) and ACCUMULATE into the
+ * grid's tallies. Each packet's random stream depends only on (seed, id),
+ * never on the launch shape. records (device, may be NULL) receives
+ * records[id - first_id]. stats (host, may be NULL): when given, the call
+ * synchronises `s` and returns this run's counters, and returns
+ * KRL_ERR_BUDGET if any packet exhausted max_iters. n = 0 is a no-op.
+ */
+KRL_API krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t seed,
+                           const krl_tune* tune, krl_packet_record* records,
+                           krl_run_stats* stats, krl_stream s);
+
+/* ------------------------------------------------------------------ tallies */
+
+typedef enum {
+    KRL_OUT_SPEC_W = 0,   /* double [spec_nbins + 2]: under, bins, over (weights)   */
+    KRL_OUT_SPEC_N = 1,   /* uint64 [spec_nbins + 2]: packet counts               */
+    KRL_OUT_SCATMAP = 2,  /* uint64 [ncell]: scatterings per cell                  */
+    KRL_OUT_EXC = 3,      /* double [ncell]: sum of w ds H(a, x_com) (ds in cells)  */
+    KRL_OUT_J = 4,        /* double [ncell][n_ch]: sum of w ds per comoving channel */
+    KRL_OUT_EMISS = 5,    /* float [n_cam][ncell][n_ch]: sum of
+                             w ds alpha0 H(a,x_in) R(x_out,k; x_in, g) / 4 pi      */
+    KRL_OUT_STATS = 6,    /* uint64 [8]: emitted, escaped, destroyed, stuck,
+                             scatterings, crossings, 0, 0 (all runs since reset)   */
+    /* read-only views of what krl_line_set built (float32 unless noted) */
+    KRL_OUT_VOIGT = 16,   /* [5000]: ln H(a, 10^l), l = -4 + 7 i / 4999           */
+    KRL_OUT_US_X = 17,    /* [40]: sampler incoming-frequency nodes |x|           */
+    KRL_OUT_US_LNCDF = 18,/* [40][251]: ln CDF of u_par at u_j = -6 + 0.048 j       */
+    KRL_OUT_RTAB = 19,    /* [40 g][200 |x|][201 Delta] R_IIA table (emissivity only) */
+    KRL_OUT_CELLS = 20,   /* float4 [ncell]: {alpha0 dx, Vx/b, Vy/b, Vz/b}         */
+    KRL_OUT_EPS = 21,     /* [ncell]: destruction probability (when k_ul, n_coll)  */
+    KRL_OUT_SRC_CDF = 22, /* double [ncell]: emission CDF (volume source)         */
+    KRL_OUT_H0 = 23       /* [1]: H(a, 0)                                          */
+} krl_tally_kind;
+
+/*
+ * Copy one accumulated tally (raw, unit packet weight, code units), or one
+ * of the line's tables / per-cell records, into the caller's device buffer
+ * dst (bytes must equal the output's size, see krl_tally_bytes).
+ * Enqueued on `s`; does not synchronise.
+ */
+KRL_API krl_status krl_tallies_get(krl_grid* g, krl_tally_kind kind, void* dst, size_t bytes,
+                           krl_stream s);
+
+/* Size in bytes of a tally (0 if it is not enabled). */
+KRL_API size_t krl_tally_bytes(const krl_grid* g, krl_tally_kind kind);
+
+/* Zero all tallies and counters. Enqueued on `s`. */
+KRL_API krl_status krl_tallies_reset(krl_grid* g, krl_stream s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRL_H */

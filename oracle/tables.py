@@ -144,7 +144,13 @@ def usampler_masses(x: float, a: float):
     lo, hi = u[:-1], u[1:]
     m = 0.5 * (lo + hi)
     h = hi - lo
-    I0 = (np.arctan((hi - x) / a) - np.arctan((lo - x) / a)) / a
+    dl, dh = lo - x, hi - x
+    # atan(dh/a) - atan(dl/a); for a cell on one side of x the difference of
+    # two near-equal angles is taken as atan(h a / (a^2 + dl dh)), which does
+    # not cancel when a is tiny
+    same_side = dl * dh > 0
+    I0 = np.where(same_side, np.arctan(np.where(same_side, h * a / (a * a + dl * dh), 0.0)),
+                  np.arctan(dh / a) - np.arctan(dl / a)) / a
     Jx = 0.5 * np.log((a * a + (hi - x) ** 2) / (a * a + (lo - x) ** 2))   # int (u - x) L du
     I1 = Jx + (x - m) * I0
     I2 = h - a * a * I0 + 2.0 * (x - m) * Jx + (x - m) ** 2 * I0

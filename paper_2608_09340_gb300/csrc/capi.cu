@@ -1,0 +1,526 @@
+// C ABI of libkrl (declared in include/krl.h): grid and line objects, the
+// packet-run entry point and tally readout. Host code only; every step of
+// the walk runs in the kernels of transport.cu and tables.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "krl_internal.cuh"
+
+using namespace krl;
+
+struct krl_grid {
+    int nx = 0, ny = 0, nz = 0, ncell = 0;
+    double cell_cm = 0.0;
+    unsigned periodic = 0;
+    int opacity_kind = 0;
+    double T_K = 0.0;
+    int device = 0;
+    int num_sms = 0;
+    // owned copies of the fields
+    float* opacity = nullptr;
+    float* vel[3] = {nullptr, nullptr, nullptr};
+    float* n_coll = nullptr;
+    bool has_vel = false;
+    // line
+    bool line_ok = false;
+    krl_line_desc line{};
+    krl_line_info info{};
+    bool has_rtab = false;
+    float4* cells = nullptr;
+    float* eps = nullptr;
+    float* src_rate = nullptr;
+    double* src_cdf = nullptr;
+    LineTables tab{};
+    // tallies
+    double* spec_w = nullptr;
+    unsigned long long* spec_c = nullptr;
+    unsigned long long* scat = nullptr;
+    double* exc = nullptr;
+    double* J = nullptr;
+    float* emiss = nullptr;
+    unsigned long long* stats = nullptr;      // cumulative [ST_N]
+    // scratch
+    unsigned long long* run_stats = nullptr;  // [ST_N] per run
+    unsigned long long* next = nullptr;       // work counter
+    int* bad = nullptr;                       // validation flags
+    double* scan_work = nullptr;
+    size_t scan_work_n = 0;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+krl_status fail(krl_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+krl_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(KRL_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(KRL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define KRL_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) return cudaSuccess;
+    return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void free_line(krl_grid* g)
+{
+    dfree(g->cells);
+    dfree(g->eps);
+    dfree(g->src_rate);
+    dfree(g->src_cdf);
+    dfree(g->tab.voigt_lnH);
+    dfree(g->tab.H0);
+    dfree(g->tab.us_x);
+    dfree(g->tab.us_lncdf);
+    dfree(g->tab.us_guide);
+    dfree(g->tab.rtab);
+    dfree(g->tab.work);
+    dfree(g->spec_w);
+    dfree(g->spec_c);
+    dfree(g->scat);
+    dfree(g->exc);
+    dfree(g->J);
+    dfree(g->emiss);
+    dfree(g->scan_work);
+    g->line_ok = false;
+}
+
+// Physical constants (CGS, CODATA 2018).
+constexpr double kKB = 1.380649e-16;
+constexpr double kC = 2.99792458e10;
+constexpr double kAmu = 1.66053906660e-24;
+constexpr double kPiD = 3.14159265358979323846;
+
+size_t tally_elems(const krl_grid* g, krl_tally_kind k, size_t* esz)
+{
+    const krl_line_desc& L = g->line;
+    size_t nb = (size_t)L.spec_nbins + 2;
+    switch (k) {
+    case KRL_OUT_SPEC_W: *esz = 8; return g->spec_w ? nb : 0;
+    case KRL_OUT_SPEC_N: *esz = 8; return g->spec_c ? nb : 0;
+    case KRL_OUT_SCATMAP: *esz = 8; return g->scat ? (size_t)g->ncell : 0;
+    case KRL_OUT_EXC: *esz = 8; return g->exc ? (size_t)g->ncell : 0;
+    case KRL_OUT_J: *esz = 8; return g->J ? (size_t)g->ncell * L.n_ch : 0;
+    case KRL_OUT_EMISS: *esz = 4; return g->emiss ? (size_t)L.n_cam * g->ncell * L.n_ch : 0;
+    case KRL_OUT_STATS: *esz = 8; return g->stats ? (size_t)ST_N : 0;
+    case KRL_OUT_VOIGT: *esz = 4; return g->tab.voigt_lnH ? (size_t)kVoigtN : 0;
+    case KRL_OUT_US_X: *esz = 4; return g->tab.us_x ? (size_t)kUsNx : 0;
+    case KRL_OUT_US_LNCDF: *esz = 4; return g->tab.us_lncdf ? (size_t)kUsNx * kUsNu : 0;
+    case KRL_OUT_RTAB: *esz = 4; return g->tab.rtab ? kRtabElems : 0;
+    case KRL_OUT_CELLS: *esz = 16; return g->cells ? (size_t)g->ncell : 0;
+    case KRL_OUT_EPS: *esz = 4; return g->eps ? (size_t)g->ncell : 0;
+    case KRL_OUT_SRC_CDF: *esz = 8; return g->src_cdf ? (size_t)g->ncell : 0;
+    case KRL_OUT_H0: *esz = 4; return g->tab.H0 ? 1 : 0;
+    }
+    *esz = 0;
+    return 0;
+}
+
+const void* tally_ptr(const krl_grid* g, krl_tally_kind k)
+{
+    switch (k) {
+    case KRL_OUT_SPEC_W: return g->spec_w;
+    case KRL_OUT_SPEC_N: return g->spec_c;
+    case KRL_OUT_SCATMAP: return g->scat;
+    case KRL_OUT_EXC: return g->exc;
+    case KRL_OUT_J: return g->J;
+    case KRL_OUT_EMISS: return g->emiss;
+    case KRL_OUT_STATS: return g->stats;
+    case KRL_OUT_VOIGT: return g->tab.voigt_lnH;
+    case KRL_OUT_US_X: return g->tab.us_x;
+    case KRL_OUT_US_LNCDF: return g->tab.us_lncdf;
+    case KRL_OUT_RTAB: return g->tab.rtab;
+    case KRL_OUT_CELLS: return g->cells;
+    case KRL_OUT_EPS: return g->eps;
+    case KRL_OUT_SRC_CDF: return g->src_cdf;
+    case KRL_OUT_H0: return g->tab.H0;
+    }
+    return nullptr;
+}
+
+krl_status zero_tallies(krl_grid* g, cudaStream_t s)
+{
+    for (int k = 0; k <= (int)KRL_OUT_STATS; ++k) {
+        size_t esz;
+        size_t n = tally_elems(g, (krl_tally_kind)k, &esz);
+        if (n) KRL_CUDA(cudaMemsetAsync((void*)tally_ptr(g, (krl_tally_kind)k), 0, n * esz, s), "zero tallies");
+    }
+    return KRL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* krl_last_error(void) { return g_err; }
+
+int krl_version(void) { return 100; }
+
+krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st)
+{
+    cudaStream_t s = (cudaStream_t)st;
+    if (!out || !d) return fail(KRL_ERR_ARG, "krl_grid_create: NULL argument");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(KRL_ERR_ARG, "grid dimensions must be >= 1");
+    long long nc = (long long)d->nx * d->ny * d->nz;
+    if (nc >= (1ll << 31)) return fail(KRL_ERR_ARG, "grid has too many cells (%lld)", nc);
+    if (!(d->cell_cm > 0.0) || !isfinite(d->cell_cm)) return fail(KRL_ERR_ARG, "cell_cm must be > 0");
+    if (!(d->T_K > 0.0) || !isfinite(d->T_K)) return fail(KRL_ERR_ARG, "T_K must be > 0");
+    if (d->opacity_kind != KRL_OPACITY_TAU && d->opacity_kind != KRL_OPACITY_NL)
+        return fail(KRL_ERR_ARG, "unknown opacity_kind %d", d->opacity_kind);
+    if (!d->opacity) return fail(KRL_ERR_ARG, "opacity field is required");
+    if (d->boundary_flags & ~7u) return fail(KRL_ERR_ARG, "unknown boundary flag bits");
+    krl_grid* g = new (std::nothrow) krl_grid();
+    if (!g) return fail(KRL_ERR_OOM, "host allocation failed");
+    g->nx = d->nx;
+    g->ny = d->ny;
+    g->nz = d->nz;
+    g->ncell = (int)nc;
+    g->cell_cm = d->cell_cm;
+    g->periodic = d->boundary_flags;
+    g->opacity_kind = d->opacity_kind;
+    g->T_K = d->T_K;
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    size_t n = (size_t)nc;
+    cudaError_t e = dalloc(&g->opacity, n);
+    const float* src[3] = {d->vx, d->vy, d->vz};
+    g->has_vel = d->vx || d->vy || d->vz;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (src[k]) e = dalloc(&g->vel[k], n);
+    if (e == cudaSuccess && d->n_coll) e = dalloc(&g->n_coll, n);
+    if (e == cudaSuccess) e = dalloc(&g->stats, ST_N);
+    if (e == cudaSuccess) e = dalloc(&g->run_stats, ST_N);
+    if (e == cudaSuccess) e = dalloc(&g->next, 1);
+    if (e == cudaSuccess) e = dalloc(&g->bad, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->opacity, d->opacity, n * 4, cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (src[k]) e = cudaMemcpyAsync(g->vel[k], src[k], n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && d->n_coll) e = cudaMemcpyAsync(g->n_coll, d->n_coll, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = validate_field(g->opacity, g->ncell, false, g->bad, s);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (g->vel[k]) e = validate_field(g->vel[k], g->ncell, true, g->bad, s);
+    if (e == cudaSuccess && g->n_coll) e = validate_field(g->n_coll, g->ncell, false, g->bad, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->stats, 0, ST_N * 8, s);
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, g->bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        krl_grid_destroy(g);
+        return cuda_fail(e, "krl_grid_create");
+    }
+    if (bad) {
+        krl_grid_destroy(g);
+        return fail(KRL_ERR_NUMERIC, "grid field holds NaN/Inf or a negative opacity/density");
+    }
+    *out = g;
+    return KRL_OK;
+}
+
+krl_status krl_grid_destroy(krl_grid* g)
+{
+    if (!g) return KRL_OK;
+    cudaDeviceSynchronize();
+    free_line(g);
+    dfree(g->opacity);
+    for (int k = 0; k < 3; ++k) dfree(g->vel[k]);
+    dfree(g->n_coll);
+    dfree(g->stats);
+    dfree(g->run_stats);
+    dfree(g->next);
+    dfree(g->bad);
+    delete g;
+    return KRL_OK;
+}
+
+krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
+{
+    cudaStream_t s = (cudaStream_t)st;
+    if (!g || !d) return fail(KRL_ERR_ARG, "krl_line_set: NULL argument");
+    if (!(d->nu0_hz > 0) || !(d->mass_amu > 0) || !(d->A_ul > 0) || !(d->g_u > 0) || !(d->g_l > 0))
+        return fail(KRL_ERR_ARG, "line constants must be > 0");
+    if (d->k_ul < 0 || !isfinite(d->k_ul)) return fail(KRL_ERR_ARG, "k_ul must be >= 0");
+    if (d->src_kind < KRL_SRC_POINT || d->src_kind > KRL_SRC_VOLUME) return fail(KRL_ERR_ARG, "unknown src_kind");
+    if (d->src_profile != KRL_PROFILE_LINE_CENTRE && d->src_profile != KRL_PROFILE_GAUSSIAN)
+        return fail(KRL_ERR_ARG, "unknown src_profile");
+    if ((d->src_kind == KRL_SRC_PLANE || d->src_kind == KRL_SRC_BEAM) && (d->src_axis < 0 || d->src_axis > 2))
+        return fail(KRL_ERR_ARG, "src_axis must be 0, 1 or 2");
+    if (d->src_kind == KRL_SRC_BEAM && d->band_axis >= 0 &&
+        (d->band_axis > 2 || d->band_axis == d->src_axis || !(d->band_hi >= d->band_lo)))
+        return fail(KRL_ERR_ARG, "bad beam band");
+    if (d->src_kind == KRL_SRC_VOLUME && !d->src_rate) return fail(KRL_ERR_ARG, "volume source needs src_rate");
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(d->src_pos[k])) return fail(KRL_ERR_ARG, "src_pos must be finite");
+    if (d->spec_nbins < 1 || !(d->spec_xmax > d->spec_xmin)) return fail(KRL_ERR_ARG, "bad spectrum binning");
+    if (d->tally_flags & ~15u) return fail(KRL_ERR_ARG, "unknown tally flag bits");
+    bool need_ch = d->tally_flags & (KRL_TALLY_J | KRL_TALLY_EMISS);
+    if (need_ch && (d->n_ch < 1 || !(d->ch_dv_cms > 0))) return fail(KRL_ERR_ARG, "channels need n_ch >= 1, dv > 0");
+    if ((d->tally_flags & KRL_TALLY_EMISS) && (d->n_cam < 1 || d->n_cam > KRL_MAX_CAMERAS))
+        return fail(KRL_ERR_ARG, "emissivity needs 1..%d cameras", KRL_MAX_CAMERAS);
+
+    free_line(g);
+    KRL_CUDA(cudaMemsetAsync(g->bad, 0, sizeof(int), s), "krl_line_set");
+    krl_line_desc L = *d;
+    if (!need_ch) L.n_ch = 0;
+    if (!(L.tally_flags & KRL_TALLY_EMISS)) L.n_cam = 0;
+    g->line = L;
+
+    // scalar line constants (Sec. 2.1, Eq. xdef, Eq. sigma0)
+    krl_line_info I{};
+    I.b_cms = sqrt(2.0 * kKB * g->T_K / (L.mass_amu * kAmu));
+    I.nu_D_hz = L.nu0_hz * I.b_cms / kC;
+    I.a = L.a_fixed > 0 ? L.a_fixed : L.A_ul / (4.0 * kPiD * I.nu_D_hz);
+    I.sigma0_cm2 = (L.g_u / L.g_l) * L.A_ul * kC * kC * kC / (8.0 * pow(kPiD, 1.5) * pow(L.nu0_hz, 3) * I.b_cms);
+    I.ncell = g->ncell;
+    g->info = I;
+
+    const size_t n = (size_t)g->ncell;
+    const bool with_r = (L.tally_flags & KRL_TALLY_EMISS) != 0;
+    const bool with_eps = L.k_ul > 0 && g->n_coll;
+    cudaError_t e = dalloc(&g->cells, n);
+    if (e == cudaSuccess && with_eps) e = dalloc(&g->eps, n);
+    if (e == cudaSuccess) e = dalloc(&g->tab.voigt_lnH, (size_t)kVoigtN);
+    if (e == cudaSuccess) e = dalloc(&g->tab.H0, 1);
+    if (e == cudaSuccess) e = dalloc(&g->tab.us_x, (size_t)kUsNx);
+    if (e == cudaSuccess) e = dalloc(&g->tab.us_lncdf, (size_t)kUsNx * kUsNu);
+    if (e == cudaSuccess) e = dalloc(&g->tab.us_guide, (size_t)kUsNx * kGuideN);
+    if (e == cudaSuccess && with_r) e = dalloc(&g->tab.rtab, kRtabElems);
+    if (e == cudaSuccess) e = dalloc(&g->tab.work, line_tables_work_doubles());
+    if (e == cudaSuccess) e = dalloc(&g->spec_w, (size_t)L.spec_nbins + 2);
+    if (e == cudaSuccess) e = dalloc(&g->spec_c, (size_t)L.spec_nbins + 2);
+    if (e == cudaSuccess && (L.tally_flags & KRL_TALLY_SCATMAP)) e = dalloc(&g->scat, n);
+    if (e == cudaSuccess && (L.tally_flags & KRL_TALLY_EXC)) e = dalloc(&g->exc, n);
+    if (e == cudaSuccess && (L.tally_flags & KRL_TALLY_J)) e = dalloc(&g->J, n * L.n_ch);
+    if (e == cudaSuccess && with_r) e = dalloc(&g->emiss, (size_t)L.n_cam * n * L.n_ch);
+    if (e == cudaSuccess && L.src_kind == KRL_SRC_VOLUME) {
+        e = dalloc(&g->src_rate, n);
+        if (e == cudaSuccess) e = dalloc(&g->src_cdf, n);
+        g->scan_work_n = emission_cdf_work_doubles(g->ncell);
+        if (e == cudaSuccess) e = dalloc(&g->scan_work, g->scan_work_n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->src_rate, L.src_rate, n * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) {
+        free_line(g);
+        return cuda_fail(e, "krl_line_set allocation");
+    }
+    g->has_rtab = with_r;
+    g->line.src_rate = g->src_rate;
+
+    FieldArgs F{};
+    F.ncell = g->ncell;
+    F.opacity_kind = g->opacity_kind;
+    F.opacity = g->opacity;
+    F.vx = g->vel[0];
+    F.vy = g->vel[1];
+    F.vz = g->vel[2];
+    F.n_coll = g->n_coll;
+    F.tau_scale = g->opacity_kind == KRL_OPACITY_NL ? I.sigma0_cm2 * g->cell_cm : 1.0;
+    F.inv_b = 1.0 / I.b_cms;
+    F.k_ul = L.k_ul;
+    F.A_ul = L.A_ul;
+    F.cells = g->cells;
+    F.eps = g->eps;
+    e = derive_fields(F, s);
+    if (e == cudaSuccess) e = build_line_tables(I.a, g->tab, with_r, s);
+    if (e == cudaSuccess && L.src_kind == KRL_SRC_VOLUME)
+        e = emission_cdf(g->src_rate, g->ncell, g->src_cdf, g->scan_work, g->scan_work_n, g->bad, s);
+    if (e != cudaSuccess) {
+        free_line(g);
+        return cuda_fail(e, "krl_line_set kernels");
+    }
+    krl_status zs = zero_tallies(g, s);
+    if (zs != KRL_OK) return zs;
+    // H(a, 0) for krl_line_info_get (small synchronous copy on this stream)
+    float h0 = 0.0f;
+    e = cudaMemcpyAsync(&h0, g->tab.H0, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "krl_line_set");
+    int bad = 0;
+    cudaMemcpy(&bad, g->bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (bad & 2) {
+        free_line(g);
+        return fail(KRL_ERR_ARG, "volume source rate sums to zero");
+    }
+    if (bad) {
+        free_line(g);
+        return fail(KRL_ERR_NUMERIC, "volume source rate holds NaN/Inf or a negative value");
+    }
+    g->info.H0 = h0;
+    g->line_ok = true;
+    return KRL_OK;
+}
+
+krl_status krl_line_info_get(const krl_grid* g, krl_line_info* out)
+{
+    if (!g || !out) return fail(KRL_ERR_ARG, "krl_line_info_get: NULL argument");
+    if (!g->line_ok) return fail(KRL_ERR_STATE, "no line set");
+    *out = g->info;
+    return KRL_OK;
+}
+
+krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t seed, const krl_tune* tune,
+                           krl_packet_record* records, krl_run_stats* stats, krl_stream st)
+{
+    cudaStream_t s = (cudaStream_t)st;
+    if (!g) return fail(KRL_ERR_ARG, "krl_run_packets: NULL grid");
+    if (!g->line_ok) return fail(KRL_ERR_STATE, "krl_run_packets before krl_line_set");
+    krl_tune T{KRL_PREC_FP32, 256, 0, 1, 1ull << 40};
+    if (tune) {
+        if (tune->precision != KRL_PREC_FP32 && tune->precision != KRL_PREC_FP64)
+            return fail(KRL_ERR_ARG, "unknown precision");
+        T.precision = tune->precision;
+        if (tune->block) T.block = tune->block;
+        if (tune->ctas_per_sm) T.ctas_per_sm = tune->ctas_per_sm;
+        if (tune->refill_min) T.refill_min = tune->refill_min;
+        if (tune->max_iters) T.max_iters = tune->max_iters;
+    }
+    if (T.block < 32 || T.block > 256 || T.block % 32) return fail(KRL_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
+    if (T.refill_min < 1 || T.refill_min > 32) return fail(KRL_ERR_ARG, "refill_min must be in [1, 32]");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (n == 0) return KRL_OK;
+
+    const krl_line_desc& L = g->line;
+    unsigned f = 0;
+    if (g->has_vel) f |= F_VEL;
+    if (L.tally_flags & KRL_TALLY_SCATMAP) f |= F_SCAT;
+    unsigned rich = L.tally_flags & (KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS);
+    if (g->eps) rich |= kRichEps;
+    if (rich) f |= F_RICH;
+
+    int occ = transport_occupancy(T.precision, f, T.block);
+    if (occ < 1) return fail(KRL_ERR_CUDA, "transport kernel cannot be resident at block %d", T.block);
+    int per_sm = T.ctas_per_sm > 0 ? (T.ctas_per_sm < occ ? T.ctas_per_sm : occ) : occ;
+    int grid = g->num_sms * per_sm;
+
+    TransportArgs A{};
+    A.cells = g->cells;
+    A.eps = g->eps;
+    A.nx = g->nx;
+    A.ny = g->ny;
+    A.nz = g->nz;
+    A.ncell = g->ncell;
+    A.periodic = g->periodic;
+    A.a = (float)g->info.a;
+    A.H0 = g->tab.H0;
+    A.voigt_lnH = g->tab.voigt_lnH;
+    A.us_x = g->tab.us_x;
+    A.us_lncdf = g->tab.us_lncdf;
+    A.us_guide = g->tab.us_guide;
+    A.rtab = g->tab.rtab;
+    A.src_kind = L.src_kind;
+    A.src_profile = L.src_profile;
+    A.src_axis = L.src_axis;
+    A.band_axis = L.band_axis;
+    for (int k = 0; k < 3; ++k) A.src_pos[k] = L.src_pos[k];
+    A.src_plane = L.src_plane;
+    A.band_lo = L.band_lo;
+    A.band_hi = L.band_hi;
+    A.src_cdf = g->src_cdf;
+    A.spec_lo = L.spec_xmin;
+    A.spec_hi = L.spec_xmax;
+    A.spec_n = L.spec_nbins;
+    A.n_ch = L.n_ch;
+    A.ch_x0 = (float)(L.ch_vmin_cms / g->info.b_cms);
+    A.ch_dx = (float)(L.ch_dv_cms / g->info.b_cms);
+    A.n_cam = L.n_cam;
+    for (int m = 0; m < L.n_cam; ++m) {
+        double th = L.cam_theta[m], ph = L.cam_phi[m];
+        A.cam[m][0] = (float)(sin(th) * cos(ph));
+        A.cam[m][1] = (float)(sin(th) * sin(ph));
+        A.cam[m][2] = (float)cos(th);
+    }
+    A.rich = rich;
+    A.spec_w = g->spec_w;
+    A.spec_c = g->spec_c;
+    A.scat = g->scat;
+    A.exc = g->exc;
+    A.J = g->J;
+    A.emiss = g->emiss;
+    A.stats = g->run_stats;
+    A.next = g->next;
+    A.rec = records;
+    A.first = first_id;
+    A.n = n;
+    A.k0 = (unsigned)(seed & 0xffffffffu);
+    A.k1 = (unsigned)(seed >> 32);
+    A.max_iters = T.max_iters;
+    A.refill_min = T.refill_min;
+
+    KRL_CUDA(cudaMemsetAsync(g->next, 0, sizeof(unsigned long long), s), "reset work counter");
+    KRL_CUDA(cudaMemsetAsync(g->run_stats, 0, ST_N * sizeof(unsigned long long), s), "reset run counters");
+    KRL_CUDA(launch_transport(A, T.precision, f, grid, T.block, s), "transport launch");
+    KRL_CUDA(add_counters(g->stats, g->run_stats, ST_N, s), "accumulate counters");
+    if (stats) {
+        unsigned long long h[ST_N];
+        KRL_CUDA(cudaMemcpyAsync(h, g->run_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "read counters");
+        KRL_CUDA(cudaStreamSynchronize(s), "krl_run_packets");
+        stats->emitted = h[ST_EMITTED];
+        stats->escaped = h[ST_ESCAPED];
+        stats->destroyed = h[ST_DESTROYED];
+        stats->stuck = h[ST_STUCK];
+        stats->scatterings = h[ST_SCAT];
+        stats->crossings = h[ST_CROSS];
+        if (h[ST_STUCK]) return fail(KRL_ERR_BUDGET, "%llu packets exhausted max_iters", h[ST_STUCK]);
+    }
+    return KRL_OK;
+}
+
+size_t krl_tally_bytes(const krl_grid* g, krl_tally_kind kind)
+{
+    if (!g || !g->line_ok) return 0;
+    size_t esz;
+    size_t n = tally_elems(g, kind, &esz);
+    return n * esz;
+}
+
+krl_status krl_tallies_get(krl_grid* g, krl_tally_kind kind, void* dst, size_t bytes, krl_stream st)
+{
+    if (!g || !dst) return fail(KRL_ERR_ARG, "krl_tallies_get: NULL argument");
+    if (!g->line_ok) return fail(KRL_ERR_STATE, "no line set");
+    size_t esz;
+    size_t n = tally_elems(g, kind, &esz);
+    if (n == 0) return fail(KRL_ERR_ARG, "tally %d is not enabled", (int)kind);
+    if (bytes != n * esz) return fail(KRL_ERR_ARG, "tally %d needs %zu bytes, got %zu", (int)kind, n * esz, bytes);
+    KRL_CUDA(cudaMemcpyAsync(dst, tally_ptr(g, kind), bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)st),
+             "krl_tallies_get");
+    return KRL_OK;
+}
+
+krl_status krl_tallies_reset(krl_grid* g, krl_stream st)
+{
+    if (!g) return fail(KRL_ERR_ARG, "krl_tallies_reset: NULL grid");
+    if (!g->line_ok) return fail(KRL_ERR_STATE, "no line set");
+    return zero_tallies(g, (cudaStream_t)st);
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Internal declarations shared by the CUDA translation units of libkrl.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "krl.h"
+
+namespace krl {
+
+// ---------------------------------------------------------------- table geometry
+// ph_mode 2 Voigt slice: nodes uniform in log10|x| on [-4, 3] (Sec. 2.2.1, 2.3.1).
+constexpr int kVoigtN = 5000;
+constexpr double kVoigtL0 = -4.0;
+constexpr double kVoigtL1 = 3.0;
+// Velocity sampler (Sec. 2.1.1): 40 incoming-frequency rows, 251 u-nodes.
+constexpr int kUsNx = 40;
+constexpr int kUsNu = 251;
+constexpr double kUsU0 = -6.0;
+constexpr double kUsDu = 0.048;
+constexpr double kUsFloor = 1e-30;
+// R_IIA table (Eq. riia-table): Delta x |x_in| x g.
+constexpr int kRnD = 201;
+constexpr int kRnX = 200;
+constexpr int kRnG = 40;
+constexpr double kRdMax = 10.0;
+constexpr double kRdStep = 0.1;
+constexpr double kRxMax = 120.0;
+constexpr double kRsMin = 0.1;
+constexpr size_t kRtabElems = (size_t)kRnG * kRnX * kRnD;
+
+// Search guide of the sampler rows: for each row, kGuideN bins uniform in
+// logit(xi) = ln(xi / (1 - xi)) on [-kGuideW, kGuideW]; entry m is the
+// largest node j whose CDF is <= sigmoid(left edge of bin m). A lookup starts
+// there and walks to the exact node, so the guide only shortens the search.
+constexpr int kGuideN = 128;
+constexpr double kGuideW = 16.7;
+
+// Shared-memory image of the per-line sampling tables used by the walk.
+constexpr int kSmemVoigt = 0;
+constexpr int kSmemUsX = kVoigtN;                 // 40 floats
+constexpr int kSmemUsC = kVoigtN + 48;            // 40 x 251 floats
+constexpr int kSmemFloats = kSmemUsC + kUsNx * kUsNu;
+constexpr int kSmemGuideBytes = kUsNx * kGuideN;  // uint8 after the floats
+constexpr size_t kSmemBytes = (size_t)kSmemFloats * sizeof(float) + kSmemGuideBytes;
+
+// ---------------------------------------------------------------- compile-time walk features
+enum : unsigned {
+    F_VEL = 1u,       // cells carry a bulk velocity
+    F_SCAT = 2u,      // per-cell scattering counts
+    F_RICH = 4u,      // excitation / mean intensity / emissivity / destruction
+};
+
+enum { ST_EMITTED = 0, ST_ESCAPED, ST_DESTROYED, ST_STUCK, ST_SCAT, ST_CROSS, ST_N = 8 };
+
+struct TransportArgs {
+    const float4* cells;      // {line-centre tau per cell width, Vx/b, Vy/b, Vz/b}
+    const float* eps;         // per-cell destruction probability or nullptr
+    int nx, ny, nz, ncell;
+    unsigned periodic;        // bit d set: axis d periodic
+    float a;
+    const float* H0;          // device scalar H(a, 0)
+    const float* voigt_lnH;
+    const float* us_x;
+    const float* us_lncdf;
+    const unsigned char* us_guide;
+    const float* rtab;
+    int src_kind, src_profile, src_axis, band_axis;
+    double src_pos[3];
+    double src_plane, band_lo, band_hi;
+    const double* src_cdf;
+    double spec_lo, spec_hi;
+    int spec_n;
+    int n_ch;
+    float ch_x0, ch_dx;       // v_min / b, dv / b
+    int n_cam;
+    float cam[KRL_MAX_CAMERAS][3];
+    unsigned rich;            // KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS, eps present (bit 16)
+    double* spec_w;
+    unsigned long long* spec_c;
+    unsigned long long* scat;
+    double* exc;
+    double* J;
+    float* emiss;
+    unsigned long long* stats;   // [ST_N] for this launch
+    unsigned long long* next;    // work counter, zero at launch
+    krl_packet_record* rec;
+    unsigned long long first, n;
+    unsigned k0, k1;
+    unsigned long long max_iters;
+    int refill_min;
+};
+
+constexpr unsigned kRichEps = 1u << 16;
+
+// Launch the walk (transport.cu). grid/block chosen by the caller.
+cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned features,
+                             int grid, int block, cudaStream_t s);
+// Occupancy of one instantiation (CTAs per SM at this block size).
+int transport_occupancy(int precision, unsigned features, int block);
+
+// ---------------------------------------------------------------- setup kernels (tables.cu)
+struct LineTables {
+    float* voigt_lnH;   // [kVoigtN]
+    float* H0;          // [1]
+    float* us_x;        // [kUsNx]
+    float* us_lncdf;    // [kUsNx * kUsNu]
+    unsigned char* us_guide;  // [kUsNx * kGuideN]
+    float* rtab;        // [kRtabElems]
+    double* work;       // scratch: Weideman coefficients + R-table masses
+};
+size_t line_tables_work_doubles();
+cudaError_t build_line_tables(double a, const LineTables& T, bool with_r, cudaStream_t s);
+
+struct FieldArgs {
+    int ncell;
+    int opacity_kind;
+    const float* opacity;
+    const float* vx;
+    const float* vy;
+    const float* vz;
+    const float* n_coll;
+    double tau_scale;     // sigma0 * cell_cm for KRL_OPACITY_NL, 1 for TAU
+    double inv_b;
+    double k_ul, A_ul;
+    float4* cells;
+    float* eps;           // may be nullptr
+};
+cudaError_t derive_fields(const FieldArgs& F, cudaStream_t s);
+
+// Flags bad values (NaN, Inf, negative where forbidden) into *bad (int, device).
+cudaError_t validate_field(const float* f, int n, bool allow_negative, int* bad, cudaStream_t s);
+
+// Inclusive FP64 scan of rate[n] (float), normalised by its last element.
+cudaError_t emission_cdf(const float* rate, int n, double* cdf, double* work, size_t work_doubles,
+                         int* bad, cudaStream_t s);
+size_t emission_cdf_work_doubles(int n);
+
+// out[i] += in[i], 64-bit counters.
+cudaError_t add_counters(unsigned long long* out, const unsigned long long* in, int n, cudaStream_t s);
+
+}  // namespace krl

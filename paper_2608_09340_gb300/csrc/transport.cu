@@ -1,0 +1,665 @@
+// Monte Carlo photon-packet walk (Sec. 2.1-2.3 of the paper), one persistent
+// kernel per run.
+//
+// Scheduling: a persistent grid (a few CTAs per SM). Each lane owns one
+// packet in registers. Whenever enough lanes of a warp are idle, the warp
+// takes a contiguous block of packet ids with ONE atomicAdd on a global work
+// counter (ballot + popc + shuffle) and the idle lanes emit those packets;
+// this is the server-worker scheme of Sec. 2.3.2 at warp granularity.
+//
+// Per iteration a lane advances its packet by one event in the current
+// cell: with x_com = x_lab - n.V/b (Sec. 2.2.1) and alpha = alpha0
+// H(a, x_com) (Sec. 2.1), it either scatters inside the cell (tau < alpha
+// s_exit) or crosses the nearest face. A scattering draws u_par from the
+// velocity sampler (Sec. 2.1.1), u_perp from a Gaussian, an isotropic new
+// direction and x_out = x_in + u_par (g - 1) + u_perp sin(gamma)
+// (Eq. riia-scatter); with probability epsilon (Eq. eps) the photon is
+// destroyed instead. Leaving a non-periodic face is an escape, binned in the
+// lab-frame spectrum.
+//
+// Random numbers: Philox4x32-10 with counter (id_lo, id_hi, event, block)
+// and key (seed_lo, seed_hi); a 32-bit word r becomes ((r >> 9) + 1/2) 2^-23,
+// exact in FP32 and FP64. Event 0 is the emission, event e >= 1 the e-th
+// scattering; the slots of each event are fixed (see emit / scatter), so a
+// packet's stream depends only on (seed, id).
+//
+// Tallies: scattering counts and excitation are summed in registers over a
+// cell visit and flushed with one atomic when the packet leaves the cell;
+// the mean-intensity and emissivity tallies (Eq. scat-line) are added per
+// segment. Spectrum and counters go to FP64 / 64-bit integers.
+//
+// Precision: R = float is the production walk (FP32 arithmetic in cell-local
+// coordinates, so positions keep 2^-24 of a cell width at any optical depth);
+// R = double runs the same steps in FP64 for lockstep checks.
+#include <math.h>
+#include <stdint.h>
+
+#include "krl_internal.cuh"
+
+namespace krl {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- Philox4x32-10
+
+struct Words {
+    uint32_t w[4];
+};
+
+__device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t h0 = __umulhi(m0, c0), l0 = m0 * c0;
+        uint32_t h1 = __umulhi(m1, c2), l1 = m1 * c2;
+        uint32_t n0 = h1 ^ c1 ^ k0;
+        uint32_t n2 = h0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = l1;
+        c2 = n2;
+        c3 = l0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return Words{{c0, c1, c2, c3}};
+}
+
+// ---------------------------------------------------------------- precision policy
+
+template <typename R>
+struct Ops;
+
+template <>
+struct Ops<float> {
+    static __device__ __forceinline__ float uni(uint32_t r) { return (float)(r >> 9) * 0x1p-23f + 0x1p-24f; }
+    static __device__ __forceinline__ float ln(float v) { return __logf(v); }
+    static __device__ __forceinline__ float lg10(float v) { return __log2f(v) * 0.30102999566398120f; }
+    static __device__ __forceinline__ float ex(float v) { return __expf(v); }
+    static __device__ __forceinline__ float sq(float v) { return sqrtf(v); }
+    static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    // sin and cos of 2 pi u for u in (0, 1): shift to [-pi, pi] where the
+    // hardware approximation is accurate, then reflect.
+    static __device__ __forceinline__ void sc2pi(float u, float* s, float* c)
+    {
+        float ss, cc;
+        __sincosf(6.28318530717958648f * (u - 0.5f), &ss, &cc);
+        *s = -ss;
+        *c = -cc;
+    }
+    static __device__ __forceinline__ float big() { return 3.0e38f; }
+};
+
+template <>
+struct Ops<double> {
+    static __device__ __forceinline__ double uni(uint32_t r) { return (double)(r >> 9) * 0x1p-23 + 0x1p-24; }
+    static __device__ __forceinline__ double ln(double v) { return log(v); }
+    static __device__ __forceinline__ double lg10(double v) { return log10(v); }
+    static __device__ __forceinline__ double ex(double v) { return exp(v); }
+    static __device__ __forceinline__ double sq(double v) { return sqrt(v); }
+    static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+    static __device__ __forceinline__ void sc2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+    static __device__ __forceinline__ double big() { return 1.0e300; }
+};
+
+// ---------------------------------------------------------------- table lookups (shared memory)
+
+// H(a, x) from the ph_mode 2 slice: ln H linear in log10|x| between nodes.
+template <typename R>
+__device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
+{
+    using O = Ops<R>;
+    R ax = fabs(x);
+    if (ax < (R)1e-4) return H0;
+    if (ax > (R)1e3) return a / ((R)1.7724538509055160 * ax * ax) * ((R)1 + (R)1.5 / (ax * ax));
+    R t = (O::lg10(ax) - (R)kVoigtL0) * (R)((kVoigtN - 1) / (kVoigtL1 - kVoigtL0));
+    int i = (int)t;
+    i = i < 0 ? 0 : (i > kVoigtN - 2 ? kVoigtN - 2 : i);
+    R f = t - (R)i;
+    R l0 = (R)sv[i], l1 = (R)sv[i + 1];
+    return O::ex(((R)1 - f) * l0 + f * l1);
+}
+
+// Largest row i in [0, 38] with X[i] <= ax (closed-form guess, then fix-up).
+template <typename R>
+__device__ __forceinline__ int us_row(R ax, const float* sx)
+{
+    int i;
+    if (ax < (R)8) i = (int)(ax * (R)2.25);
+    else i = 18 + (int)((R)21 * Ops<R>::ln(ax * (R)0.125) * (R)0.27588297880498553);  // 1/ln(37.5)
+    i = i < 0 ? 0 : (i > kUsNx - 2 ? kUsNx - 2 : i);
+    if (i > 0 && (R)sx[i] > ax) --i;
+    if (i > 0 && (R)sx[i] > ax) --i;
+    if (i < kUsNx - 2 && (R)sx[i + 1] <= ax) ++i;
+    if (i < kUsNx - 2 && (R)sx[i + 1] <= ax) ++i;
+    return i;
+}
+
+// Invert one ln-CDF row at L = ln(xi): the largest node j in [0, 249] with
+// c[j] <= L, then linear interpolation of u between nodes j and j + 1. The
+// guide entry for logit(xi) gives a start at or next to j; the two bounded
+// walks make the result exactly the bisection's.
+template <typename R>
+__device__ __forceinline__ R us_invert(const float* row, const unsigned char* gd, int m, R L)
+{
+    int j = gd[m];
+    while (j > 0 && (R)row[j] > L) --j;
+    while (j < kUsNu - 2 && (R)row[j + 1] <= L) ++j;
+    R c0 = (R)row[j], c1 = (R)row[j + 1];
+    return (R)kUsU0 + (R)kUsDu * (R)j + (R)kUsDu * Ops<R>::dv(L - c0, c1 - c0);
+}
+
+// u_par for incoming gas-frame frequency x (|x| <= 300) from uniform xi.
+template <typename R>
+__device__ __forceinline__ R us_sample(R x, R xi, const float* sx, const float* sc, const unsigned char* sg)
+{
+    using O = Ops<R>;
+    R ax = fabs(x);
+    int i = us_row(ax, sx);
+    R x0 = (R)sx[i], x1 = (R)sx[i + 1];
+    R t = O::dv(ax - x0, x1 - x0);
+    // L < 0 strictly (xi < 1), so node 250 (ln CDF = 0) always bounds the search
+    R L = fmin(O::ln(xi), (R)-1e-30);
+    R w = L - O::ln((R)1 - xi);
+    int m = (int)((w + (R)kGuideW) * (R)(kGuideN / (2.0 * kGuideW)));
+    m = m < 0 ? 0 : (m > kGuideN - 1 ? kGuideN - 1 : m);
+    R u0 = us_invert(sc + i * kUsNu, sg + i * kGuideN, m, L);
+    R u1 = us_invert(sc + (i + 1) * kUsNu, sg + (i + 1) * kGuideN, m, L);
+    R u = ((R)1 - t) * u0 + t * u1;
+    return x < (R)0 ? -u : u;
+}
+
+// ---------------------------------------------------------------- packet state
+
+template <typename R>
+struct Pkt {
+    int cx, cy, cz, c;
+    R px, py, pz;
+    R nx, ny, nz;
+    R ix, iy, iz;          // 1 / n
+    R x, tau;
+    float4 rec;            // current cell record
+    uint32_t nscat, ncross, cell0;
+    unsigned long long id;
+    uint32_t vis_scat;     // scatterings in this cell visit
+    R vis_exc;             // sum ds H over this cell visit
+};
+
+template <typename R>
+__device__ __forceinline__ void set_dir(Pkt<R>& p, R nx, R ny, R nz)
+{
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.ix = Ops<R>::rcp(nx);
+    p.iy = Ops<R>::rcp(ny);
+    p.iz = Ops<R>::rcp(nz);
+}
+
+template <typename R>
+__device__ __forceinline__ void iso_dir(R umu, R uphi, R& nx, R& ny, R& nz)
+{
+    R mu = (R)2 * umu - (R)1;
+    R st = Ops<R>::sq(fmax((R)0, (R)1 - mu * mu));
+    R s, c;
+    Ops<R>::sc2pi(uphi, &s, &c);
+    nx = st * c;
+    ny = st * s;
+    nz = mu;
+}
+
+__device__ __forceinline__ void spectrum_add(const TransportArgs& A, double x)
+{
+    int b;
+    if (x < A.spec_lo) b = 0;
+    else if (x >= A.spec_hi) b = A.spec_n + 1;
+    else {
+        b = 1 + (int)floor((x - A.spec_lo) / (A.spec_hi - A.spec_lo) * A.spec_n);
+        if (b > A.spec_n) b = A.spec_n;
+    }
+    atomicAdd(A.spec_w + b, 1.0);
+    atomicAdd(A.spec_c + b, 1ull);
+}
+
+template <typename R>
+__device__ __forceinline__ void write_record(const TransportArgs& A, const Pkt<R>& p, uint16_t status)
+{
+    if (!A.rec) return;
+    krl_packet_record r;
+    r.x = (float)p.x;
+    r.nscat = p.nscat;
+    r.ncross = p.ncross;
+    r.status = status;
+    r.pad = 0;
+    r.cell0 = p.cell0;
+    A.rec[p.id - A.first] = r;
+}
+
+// Emission (event 0). Slots: block 0 = {mu, phi, tau, freq1},
+// block 1 = {freq2, pos_a, pos_b, pos_c}, block 2 = {cell_hi, cell_lo}.
+// Returns false if the source point lies outside the domain (the packet
+// then leaves at once).
+template <typename R, unsigned F>
+__device__ bool emit(const TransportArgs& A, Pkt<R>& p)
+{
+    using O = Ops<R>;
+    const uint32_t lo = (uint32_t)p.id, hi = (uint32_t)(p.id >> 32);
+    Words b0 = philox(lo, hi, 0u, 0u, A.k0, A.k1);
+    const bool need1 = A.src_kind != KRL_SRC_POINT || A.src_profile == KRL_PROFILE_GAUSSIAN;
+    Words b1 = {{0u, 0u, 0u, 0u}};
+    if (need1) b1 = philox(lo, hi, 0u, 1u, A.k0, A.k1);
+    const int dims[3] = {A.nx, A.ny, A.nz};
+    double X[3];
+    R n[3];
+    if (A.src_kind == KRL_SRC_BEAM) {
+        n[0] = n[1] = n[2] = (R)0;
+        n[A.src_axis] = (R)1;
+        double pos[2] = {(double)O::uni(b1.w[1]), (double)O::uni(b1.w[2])};
+        int q = 0;
+        for (int d = 0; d < 3; ++d) {
+            if (d == A.src_axis) { X[d] = 0.0; continue; }
+            X[d] = (d == A.band_axis) ? A.band_lo + (A.band_hi - A.band_lo) * pos[q] : dims[d] * pos[q];
+            ++q;
+        }
+    } else {
+        iso_dir<R>(O::uni(b0.w[0]), O::uni(b0.w[1]), n[0], n[1], n[2]);
+        if (A.src_kind == KRL_SRC_POINT) {
+            X[0] = A.src_pos[0];
+            X[1] = A.src_pos[1];
+            X[2] = A.src_pos[2];
+        } else if (A.src_kind == KRL_SRC_PLANE) {
+            int q = 1;
+            for (int d = 0; d < 3; ++d)
+                X[d] = (d == A.src_axis) ? A.src_plane : dims[d] * (double)O::uni(b1.w[q++]);
+        } else {
+            Words b2 = philox(lo, hi, 0u, 2u, A.k0, A.k1);
+            double uc = (double)(b2.w[0] >> 8) * 0x1p-24 + (double)(b2.w[1] >> 8) * 0x1p-48 + 0x1p-49;
+            int l = 0, h = A.ncell - 1;              // first cell with cdf > uc
+            while (l < h) {
+                int m = (l + h) >> 1;
+                if (A.src_cdf[m] > uc) h = m;
+                else l = m + 1;
+            }
+            int cz = l / (A.nx * A.ny);
+            int cy = (l / A.nx) % A.ny;
+            int cx = l % A.nx;
+            X[0] = cx + (double)O::uni(b1.w[1]);
+            X[1] = cy + (double)O::uni(b1.w[2]);
+            X[2] = cz + (double)O::uni(b1.w[3]);
+        }
+    }
+    set_dir(p, n[0], n[1], n[2]);
+    int ci[3];
+    R pp[3];
+    bool inside = true;
+    for (int d = 0; d < 3; ++d) {
+        double f = floor(X[d]);
+        int c = (int)f;
+        double q = X[d] - f;
+        if (q == 0.0 && n[d] < (R)0) {
+            c -= 1;
+            q = 1.0;
+        }
+        if ((A.periodic >> d) & 1u) {
+            c %= dims[d];
+            if (c < 0) c += dims[d];
+        }
+        if (c < 0 || c >= dims[d]) inside = false;
+        ci[d] = c;
+        pp[d] = (R)q;
+    }
+    p.tau = fmax((R)0, -O::ln(O::uni(b0.w[2])));
+    R xcom = (R)0;
+    if (A.src_profile == KRL_PROFILE_GAUSSIAN) {
+        R s, c;
+        O::sc2pi(O::uni(b1.w[0]), &s, &c);
+        xcom = O::sq(fmax((R)0, -O::ln(O::uni(b0.w[3])))) * c;
+    }
+    p.nscat = 0;
+    p.ncross = 0;
+    p.vis_scat = 0;
+    p.vis_exc = (R)0;
+    if (!inside) {
+        p.x = xcom;
+        p.cell0 = 0xFFFFFFFFu;
+        return false;
+    }
+    p.cx = ci[0];
+    p.cy = ci[1];
+    p.cz = ci[2];
+    p.px = pp[0];
+    p.py = pp[1];
+    p.pz = pp[2];
+    p.c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
+    p.cell0 = (uint32_t)p.c;
+    p.rec = __ldg(A.cells + p.c);
+    R vdn = (F & F_VEL) ? p.nx * (R)p.rec.y + p.ny * (R)p.rec.z + p.nz * (R)p.rec.w : (R)0;
+    p.x = xcom + vdn;
+    return true;
+}
+
+// Per-segment tallies of the rich mode: mean intensity by comoving channel
+// and the camera-directed emissivity (Eq. scat-line with the trilinear
+// R_IIA table, Eq. riia-table, or Eq. riia-inf for |x_in| >= 120).
+template <typename R, unsigned F>
+__device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xcom, R H)
+{
+    if ((A.rich & KRL_TALLY_J) && A.n_ch > 0) {
+        R q = (-xcom - (R)A.ch_x0) / (R)A.ch_dx;
+        if (q >= (R)0 && q < (R)A.n_ch) atomicAdd(A.J + (size_t)p.c * A.n_ch + (int)q, (double)ds);
+    }
+    if (!(A.rich & KRL_TALLY_EMISS) || A.n_ch <= 0) return;
+    const R base = ds * (R)p.rec.x * H * (R)0.079577471545947668;   // 1 / 4 pi
+    const R axc = fabs(xcom);
+    const R sgn = xcom < (R)0 ? (R)-1 : (R)1;    // R(D; -x, g) = R(-D; x, g)
+    for (int m = 0; m < A.n_cam; ++m) {
+        const R cx = (R)A.cam[m][0], cy = (R)A.cam[m][1], cz = (R)A.cam[m][2];
+        R g = p.nx * cx + p.ny * cy + p.nz * cz;
+        g = fmin((R)1, fmax((R)-1, g));
+        R vc = (F & F_VEL) ? cx * (R)p.rec.y + cy * (R)p.rec.z + cz * (R)p.rec.w : (R)0;
+        // channels with |x_out,k - x_com| <= 10, x_out,k = -(x0 + (k + 1/2) dx) - vc
+        R ctr = (-(R)A.ch_x0 - vc - xcom) / (R)A.ch_dx - (R)0.5;
+        R span = (R)kRdMax / (R)A.ch_dx;
+        int k0 = (int)ceil(ctr - span) - 1;
+        int k1 = (int)floor(ctr + span) + 1;
+        k0 = k0 < 0 ? 0 : k0;
+        k1 = k1 > A.n_ch - 1 ? A.n_ch - 1 : k1;
+        if (k0 > k1) continue;
+        float* out = A.emiss + ((size_t)m * A.ncell + p.c) * A.n_ch;
+        if (axc >= (R)kRxMax) {
+            R v = fmax((R)1 - g, (R)(kRsMin * kRsMin));
+            R inv2v = (R)0.5 / v;
+            R nrm = (R)1 / Ops<R>::sq((R)6.283185307179586 * v);
+            for (int k = k0; k <= k1; ++k) {
+                R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - vc;
+                R D = xo - xcom;
+                if (fabs(D) > (R)kRdMax) continue;
+                atomicAdd(out + k, (float)(base * nrm * Ops<R>::ex(-D * D * inv2v)));
+            }
+            continue;
+        }
+        R fx = axc * (R)((kRnX - 1) / kRxMax);
+        R fg = (g + (R)1) * (R)((kRnG - 1) / 2.0);
+        int j = (int)fx;
+        int kg = (int)fg;
+        j = j > kRnX - 2 ? kRnX - 2 : j;
+        kg = kg > kRnG - 2 ? kRnG - 2 : kg;
+        R wx = fx - (R)j, wg = fg - (R)kg;
+        const float* r00 = A.rtab + ((size_t)kg * kRnX + j) * kRnD;
+        const float* r01 = r00 + kRnD;
+        const float* r10 = r00 + (size_t)kRnX * kRnD;
+        const float* r11 = r10 + kRnD;
+        R w00 = ((R)1 - wg) * ((R)1 - wx), w01 = ((R)1 - wg) * wx;
+        R w10 = wg * ((R)1 - wx), w11 = wg * wx;
+        for (int k = k0; k <= k1; ++k) {
+            R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - vc;
+            R D = xo - xcom;
+            if (fabs(D) > (R)kRdMax) continue;
+            R Dd = sgn * D;
+            R fd = (Dd + (R)kRdMax) * (R)(1.0 / kRdStep);
+            int i = (int)floor(fd);
+            i = i < 0 ? 0 : (i > kRnD - 2 ? kRnD - 2 : i);
+            R wd = fd - (R)i;
+            R a0 = w00 * (R)__ldg(r00 + i) + w01 * (R)__ldg(r01 + i) + w10 * (R)__ldg(r10 + i) + w11 * (R)__ldg(r11 + i);
+            R a1 = w00 * (R)__ldg(r00 + i + 1) + w01 * (R)__ldg(r01 + i + 1) + w10 * (R)__ldg(r10 + i + 1) +
+                   w11 * (R)__ldg(r11 + i + 1);
+            R val = ((R)1 - wd) * a0 + wd * a1;
+            atomicAdd(out + k, (float)(base * val));
+        }
+    }
+}
+
+template <typename R, unsigned F>
+__device__ __forceinline__ void flush_visit(const TransportArgs& A, Pkt<R>& p)
+{
+    if ((F & F_SCAT) && p.vis_scat) atomicAdd(A.scat + p.c, (unsigned long long)p.vis_scat);
+    if ((F & F_RICH) && (A.rich & KRL_TALLY_EXC) && p.vis_exc != (R)0) atomicAdd(A.exc + p.c, (double)p.vis_exc);
+    p.vis_scat = 0;
+    p.vis_exc = (R)0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+template <typename R, unsigned F>
+__global__ void __launch_bounds__(256) k_transport(const TransportArgs A)
+{
+    using O = Ops<R>;
+    extern __shared__ float sm[];
+    for (int i = threadIdx.x; i < kVoigtN; i += blockDim.x) sm[kSmemVoigt + i] = A.voigt_lnH[i];
+    for (int i = threadIdx.x; i < kUsNx; i += blockDim.x) sm[kSmemUsX + i] = A.us_x[i];
+    for (int i = threadIdx.x; i < kUsNx * kUsNu; i += blockDim.x) sm[kSmemUsC + i] = A.us_lncdf[i];
+    unsigned char* sgw = reinterpret_cast<unsigned char*>(sm + kSmemFloats);
+    for (int i = threadIdx.x; i < kUsNx * kGuideN; i += blockDim.x) sgw[i] = A.us_guide[i];
+    __syncthreads();
+    const float* sv = sm + kSmemVoigt;
+    const float* sx = sm + kSmemUsX;
+    const float* sc = sm + kSmemUsC;
+    const unsigned char* sg = sgw;
+
+    const R a = (R)A.a;
+    const R H0 = (R)__ldg(A.H0);
+    const unsigned lane = threadIdx.x & 31u;
+    const int dims[3] = {A.nx, A.ny, A.nz};
+
+    Pkt<R> p;
+    bool active = false;
+    bool exhausted = false;
+    unsigned long long st[ST_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    for (;;) {
+        // ---- warp-level refill: one atomic per warp, ids compacted into idle lanes
+        if (!exhausted) {
+            unsigned idle = __ballot_sync(kFull, !active);
+            int nidle = __popc(idle);
+            if (nidle == 32 || nidle >= A.refill_min) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(A.next, (unsigned long long)nidle);
+                base = __shfl_sync(kFull, base, 0);
+                if (base + (unsigned long long)nidle >= A.n) exhausted = true;
+                if (!active) {
+                    unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
+                    if (k < A.n) {
+                        p.id = A.first + k;
+                        ++st[ST_EMITTED];
+                        if (emit<R, F>(A, p)) {
+                            active = true;
+                        } else {
+                            spectrum_add(A, (double)p.x);
+                            ++st[ST_ESCAPED];
+                            write_record(A, p, 1);
+                        }
+                    }
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (!active) continue;
+
+        // ---- one event in the current cell
+        if ((unsigned long long)p.nscat + p.ncross >= A.max_iters) {
+            flush_visit<R, F>(A, p);
+            ++st[ST_STUCK];
+            st[ST_SCAT] += p.nscat;
+            st[ST_CROSS] += p.ncross;
+            write_record(A, p, 3);
+            active = false;
+            continue;
+        }
+        const R vdn = (F & F_VEL) ? p.nx * (R)p.rec.y + p.ny * (R)p.rec.z + p.nz * (R)p.rec.w : (R)0;
+        const R xcom = p.x - vdn;
+        const R H = voigt<R>(xcom, sv, a, H0);
+        const R alpha = (R)p.rec.x * H;
+        const R BIG = O::big();
+        R tx = p.nx > (R)0 ? ((R)1 - p.px) * p.ix : (p.nx < (R)0 ? -p.px * p.ix : BIG);
+        R ty = p.ny > (R)0 ? ((R)1 - p.py) * p.iy : (p.ny < (R)0 ? -p.py * p.iy : BIG);
+        R tz = p.nz > (R)0 ? ((R)1 - p.pz) * p.iz : (p.nz < (R)0 ? -p.pz * p.iz : BIG);
+        R sx_ = tx;
+        int axis = 0;
+        if (ty < sx_) { sx_ = ty; axis = 1; }
+        if (tz < sx_) { sx_ = tz; axis = 2; }
+        const bool scat = p.tau < alpha * sx_;
+        const R ds = scat ? O::dv(p.tau, alpha) : sx_;
+        p.px = fmin((R)1, fmax((R)0, p.px + ds * p.nx));
+        p.py = fmin((R)1, fmax((R)0, p.py + ds * p.ny));
+        p.pz = fmin((R)1, fmax((R)0, p.pz + ds * p.nz));
+        if (F & F_RICH) {
+            if (A.rich & KRL_TALLY_EXC) p.vis_exc += ds * H;
+            if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H);
+        }
+        if (scat) {
+            // ---- scattering (event e = nscat): block 0 = {u_par, bm_r, bm_phi, tau},
+            //      block 1 = {mu, phi, eps_test, -}
+            ++p.nscat;
+            ++p.vis_scat;
+            const uint32_t lo = (uint32_t)p.id, hi = (uint32_t)(p.id >> 32);
+            Words w0 = philox(lo, hi, p.nscat, 0u, A.k0, A.k1);
+            Words w1 = philox(lo, hi, p.nscat, 1u, A.k0, A.k1);
+            if ((F & F_RICH) && (A.rich & kRichEps)) {
+                if (O::uni(w1.w[2]) < (R)__ldg(A.eps + p.c)) {
+                    flush_visit<R, F>(A, p);
+                    ++st[ST_DESTROYED];
+                    st[ST_SCAT] += p.nscat;
+                    st[ST_CROSS] += p.ncross;
+                    write_record(A, p, 2);
+                    active = false;
+                    continue;
+                }
+            }
+            R bs, bc;
+            O::sc2pi(O::uni(w0.w[2]), &bs, &bc);
+            const R rad = O::sq(fmax((R)0, -O::ln(O::uni(w0.w[1]))));
+            const R z1 = rad * bc, z2 = rad * bs;
+            const R upar = fabs(xcom) > (R)300 ? z2 : us_sample<R>(xcom, O::uni(w0.w[0]), sx, sc, sg);
+            R mx, my, mz;
+            iso_dir<R>(O::uni(w1.w[0]), O::uni(w1.w[1]), mx, my, mz);
+            const R g = p.nx * mx + p.ny * my + p.nz * mz;
+            const R sg = O::sq(fmax((R)0, (R)1 - g * g));
+            const R xout = xcom + upar * (g - (R)1) + z1 * sg;
+            set_dir(p, mx, my, mz);
+            const R vdo = (F & F_VEL) ? mx * (R)p.rec.y + my * (R)p.rec.z + mz * (R)p.rec.w : (R)0;
+            p.x = xout + vdo;
+            p.tau = fmax((R)0, -O::ln(O::uni(w0.w[3])));
+        } else {
+            // ---- cross the face on `axis`
+            p.tau -= alpha * sx_;
+            ++p.ncross;
+            flush_visit<R, F>(A, p);
+            int ci[3] = {p.cx, p.cy, p.cz};
+            R nd = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+            int step = nd > (R)0 ? 1 : -1;
+            int nc = ci[axis] + step;
+            R pnew = step > 0 ? (R)0 : (R)1;
+            if (axis == 0) p.px = pnew;
+            else if (axis == 1) p.py = pnew;
+            else p.pz = pnew;
+            if (nc < 0 || nc >= dims[axis]) {
+                if (!((A.periodic >> axis) & 1u)) {
+                    spectrum_add(A, (double)p.x);
+                    ++st[ST_ESCAPED];
+                    st[ST_SCAT] += p.nscat;
+                    st[ST_CROSS] += p.ncross;
+                    write_record(A, p, 1);
+                    active = false;
+                    continue;
+                }
+                nc = nc < 0 ? nc + dims[axis] : nc - dims[axis];
+            }
+            ci[axis] = nc;
+            p.cx = ci[0];
+            p.cy = ci[1];
+            p.cz = ci[2];
+            p.c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
+            p.rec = __ldg(A.cells + p.c);
+        }
+    }
+
+#pragma unroll
+    for (int k = 0; k < ST_N; ++k) {
+        unsigned long long v = warp_sum(st[k]);
+        if (lane == 0 && v) atomicAdd(A.stats + k, v);
+    }
+}
+
+template <typename R, unsigned F>
+cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t s)
+{
+    auto kern = k_transport<R, F>;
+    static bool configured = false;   // per instantiation, per process
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<grid, block, kSmemBytes, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename R, unsigned F>
+int occupancy_one(int block)
+{
+    auto kern = k_transport<R, F>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, kSmemBytes) != cudaSuccess) return 0;
+    return n;
+}
+
+template <typename R>
+cudaError_t dispatch(const TransportArgs& A, unsigned f, int grid, int block, cudaStream_t s)
+{
+    switch (f & 7u) {
+    case 0: return launch_one<R, 0>(A, grid, block, s);
+    case 1: return launch_one<R, 1>(A, grid, block, s);
+    case 2: return launch_one<R, 2>(A, grid, block, s);
+    case 3: return launch_one<R, 3>(A, grid, block, s);
+    case 4: return launch_one<R, 4>(A, grid, block, s);
+    case 5: return launch_one<R, 5>(A, grid, block, s);
+    case 6: return launch_one<R, 6>(A, grid, block, s);
+    default: return launch_one<R, 7>(A, grid, block, s);
+    }
+}
+
+template <typename R>
+int occ_dispatch(unsigned f, int block)
+{
+    switch (f & 7u) {
+    case 0: return occupancy_one<R, 0>(block);
+    case 1: return occupancy_one<R, 1>(block);
+    case 2: return occupancy_one<R, 2>(block);
+    case 3: return occupancy_one<R, 3>(block);
+    case 4: return occupancy_one<R, 4>(block);
+    case 5: return occupancy_one<R, 5>(block);
+    case 6: return occupancy_one<R, 6>(block);
+    default: return occupancy_one<R, 7>(block);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned features, int grid, int block,
+                             cudaStream_t s)
+{
+    return precision == KRL_PREC_FP64 ? dispatch<double>(A, features, grid, block, s)
+                                      : dispatch<float>(A, features, grid, block, s);
+}
+
+int transport_occupancy(int precision, unsigned features, int block)
+{
+    return precision == KRL_PREC_FP64 ? occ_dispatch<double>(features, block) : occ_dispatch<float>(features, block);
+}
+
+}  // namespace krl

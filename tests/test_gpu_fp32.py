@@ -1,0 +1,84 @@
+"""Production FP32 walk against the FP64 oracle at matched packet count and
+seed (the stated bar: escaped-spectrum and emissivity histograms within
+relative L1 < 2% and a two-sample chi^2 p > 0.01)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _gpu_common import agreement, chi2_two_sample, gpu_run, need_gpu, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+def test_slab_cfg1_full_config():
+    """Static slab, 64 cells, a = 1e-2, line-centre tau0 = 1e4, 1e4 packets,
+    200 bins over [-30, 30]: FP32 GPU vs oracle."""
+    krl = need_gpu()
+    p = W.slab()            # the full configuration
+    gpu = gpu_run(krl, p, krl.KRL_PREC_FP32)
+    ref = oracle.run(p, records=True)
+    ok = agreement(gpu["records"], ref["records"], strict=False)
+    assert ok.mean() > 0.95, ok.mean()
+    g, r = gpu["spec_n"][1:-1], ref["spec_c"][1:-1]
+    assert gpu["spec_n"][0] == 0 and gpu["spec_n"][-1] == 0
+    assert rel_l1(g, r) < 0.02, rel_l1(g, r)
+    stat, dof, pv = chi2_two_sample(g, r)
+    assert pv > 0.01, (stat, dof, pv)
+    # peaks near +-1.0664 (a tau0)^{1/3} = +-4.95 (loose at a tau0 = 100)
+    xc = np.linspace(-30, 30, 201)[:-1] + 0.15
+    pk = abs(xc[np.argmax(g[:100])])
+    assert abs(pk / 4.95 - 1) < 0.1
+
+
+@pytest.mark.parametrize("v", [200.0, -200.0])
+def test_moving_sphere_spectrum(v):
+    krl = need_gpu()
+    p = W.sphere(vmax_kms=v, tau0=1e5, n=32, n_packets=4000)
+    gpu = gpu_run(krl, p, krl.KRL_PREC_FP32)
+    ref = oracle.run(p, records=True)
+    ok = agreement(gpu["records"], ref["records"], strict=False)
+    assert ok.mean() > 0.8, ok.mean()
+    g, r = gpu["spec_n"], ref["spec_c"]
+    assert rel_l1(g, r) < 0.02 + 2 * (1 - ok.mean())
+    assert chi2_two_sample(g, r)[2] > 0.01
+    assert np.abs(gpu["scatmap"].astype(np.int64) - ref["scat"].astype(np.int64)).sum() \
+        <= 0.02 * ref["scat"].sum() + gpu["records"]["nscat"][~ok].sum() + ref["records"]["nscat"][~ok].sum()
+
+
+def test_emissivity_cube_fp32():
+    """Envelope with three cameras: channel spectra of the FP32 emissivity cube
+    (summed over cells) and the cell-resolved cube vs the oracle."""
+    krl = need_gpu()
+    p = W.envelope(n=16, n_ch=16, n_packets=20000)
+    gpu = gpu_run(krl, p, krl.KRL_PREC_FP32)
+    ref = oracle.run(p, records=True)
+    ok = agreement(gpu["records"], ref["records"], strict=False)
+    assert ok.mean() > 0.99, ok.mean()
+    e = gpu["emiss"].reshape(ref["emiss"].shape).astype(np.float64)
+    re_ = ref["emiss"]
+    for m in range(e.shape[0]):
+        assert rel_l1(e[m].sum(axis=0), re_[m].sum(axis=0)) < 0.02
+        assert rel_l1(e[m], re_[m]) < 0.02
+    assert rel_l1(gpu["exc"], ref["exc"]) < 0.02
+    assert rel_l1(gpu["J"].reshape(ref["J"].shape), ref["J"]) < 0.02
+
+
+def test_thin_slab_closed_form_fp32():
+    """Eq. thin-slab through the production kernel: integral within 2%, shape
+    within 2%, peak at v = -v_z."""
+    import math
+    from scipy.special import wofz
+    krl = need_gpu()
+    p = W.thin_slab(n_packets=200000)
+    gpu = gpu_run(krl, p, krl.KRL_PREC_FP32, records=False)
+    S = gpu["emiss"].reshape(1, -1, p.channels[2])[0].sum(axis=0).astype(np.float64)
+    vmin, dv, nch = p.channels
+    v = vmin + (np.arange(nch) + 0.5) * dv
+    b = gpu["info"].b_cms
+    tau_b = float(np.float32(0.01)) * wofz(1j * gpu["info"].a).real * p.shape[2]
+    xo = -(v + 1e5) / b
+    E = p.n_packets * (1 - math.exp(-tau_b)) * np.exp(-xo * xo) / math.sqrt(math.pi) / (4 * math.pi)
+    assert abs(S.sum() / E.sum() - 1) < 0.02
+    assert np.max(np.abs(S / S.sum() - E / E.sum())) / np.max(E / E.sum()) < 0.02
+    assert abs(v[np.argmax(S)] + 1e5) <= dv

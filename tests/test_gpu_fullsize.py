@@ -1,0 +1,57 @@
+"""The 64^3 tau0 = 1e6 sphere at full size, in the launch configuration the
+benchmark times: sampled packets against the oracle one by one, and
+invariants that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _gpu_common import agreement, gpu_run, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+BENCH_PACKETS = 1 << 17
+
+
+@pytest.mark.parametrize("v", [0.0, 200.0, -200.0])
+def test_sphere_full_size(v):
+    krl = need_gpu()
+    p = W.sphere(vmax_kms=v)
+    n = BENCH_PACKETS if v == 0.0 else p.n_packets
+    gpu = gpu_run(krl, p, krl.KRL_PREC_FP32, n=n)
+    s = gpu["stats"]
+    rec = gpu["records"]
+    # conservation and bookkeeping
+    assert s.emitted == n == s.escaped and s.destroyed == 0 and s.stuck == 0
+    assert int(gpu["spec_n"].sum()) == n
+    assert int(rec["nscat"].sum(dtype=np.int64)) == s.scatterings
+    assert int(rec["ncross"].sum(dtype=np.int64)) == s.crossings
+    assert int(gpu["scatmap"].sum()) == s.scatterings
+    assert np.all(rec["status"] == 1)
+    # emission cell: the source sits on the vertex (32,32,32), so every packet
+    # starts in one of the 8 cells around it
+    nz = ny = nx = 64
+    cz, cy, cx = rec["cell0"] // (nx * ny), (rec["cell0"] // nx) % ny, rec["cell0"] % nx
+    assert np.all((cx >= 31) & (cx <= 32) & (cy >= 31) & (cy <= 32) & (cz >= 31) & (cz <= 32))
+    # static: symmetric spectrum; outflow red, infall blue
+    c = gpu["spec_n"][1:-1].astype(np.float64)
+    red = c[:200].sum() / c.sum()
+    if v == 0.0:
+        assert abs(red - 0.5) < 4 * 0.5 / np.sqrt(n)
+    elif v > 0:
+        assert red > 0.9
+    else:
+        assert red < 0.1
+    # sampled packets, recomputed one by one by the oracle
+    ids = np.random.default_rng(1).choice(n, size=12, replace=False)
+    ref = np.concatenate([oracle.run(p, n=1, first=int(i), records=True, nthreads=1)["records"] for i in ids])
+    ok = agreement(rec[ids], ref, strict=False)
+    assert ok.mean() >= 0.5, ok.mean()
+    rel = np.abs(rec["nscat"][ids].astype(np.float64) / ref["nscat"] - 1)
+    assert np.median(rel) < 0.5
+    # scatterings per packet: ~ tau0 for the static sphere, far fewer with the flow
+    mean = s.scatterings / n
+    if v == 0.0:
+        assert 5e5 < mean < 3e6
+    else:
+        assert 1e4 < mean < 1e6
