@@ -6,7 +6,9 @@ One step = one krl_run_packets launch over the next PACKETS_PER_STEP packet
 ids of the 1e6-packet job (every step of the pass runs: emission, cell walk,
 scattering, tallies, escape, regeneration, counter reduction). Inputs are
 resident on the device; L2 is flushed (a 256 MiB write) before every timed
-step and the step itself is bracketed by CUDA events on the launch stream.
+step. Steps alternate between two streams so that one step's tail overlaps
+the next step's start (--serial: one stream); the K steps are bracketed by
+CUDA events, and every launch also by its own pair on its stream.
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload instead.
@@ -25,7 +27,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PACKETS_PER_STEP = 1 << 18
+PACKETS_PER_STEP = 1 << 19
 JOB_PACKETS = 1_000_000
 METRIC = "scatterings/s & packets/s (64³ τ0=1e6 sphere)"
 UNIT = "scatterings/s"
@@ -51,6 +53,8 @@ def parse():
                     help="centre-to-edge line-centre depth (1e6 is the benchmark; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serial", dest="pipeline", action="store_false",
+                    help="issue every step on one stream (no overlap of one step's tail with the next)")
     return ap.parse_args()
 
 
@@ -216,6 +220,12 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # Steps are issued alternately on two streams: a step's launch starts on
+    # the SMs that the previous step's tail (its last, longest packets) has
+    # already released, as a production job streams its batches. Each stream
+    # flushes L2 (its own 256 MiB write) before each of its steps.
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    flushes = [flush, torch.empty(256 << 20, dtype=torch.uint8, device=dev)]
     step_id = 0
     for _ in range(args.warmup):
         lo, n = shard.step_range(step_id, rank, world, B)
@@ -225,19 +235,30 @@ def main():
     barrier()
     clocks = Clocks(local)
     clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_wall = time.perf_counter()
+    t_start.record(stream)
+    for st_ in streams:
+        st_.wait_stream(stream)
     for k in range(args.steps):
-        flush.zero_()
-        lo, n = shard.step_range(step_id, rank, world, B)
-        ev[k][0].record(stream)
-        g.run(n=n, first=lo, want_stats=False)
-        ev[k][1].record(stream)
+        sk = streams[k % 2 if args.pipeline else 0]
+        with torch.cuda.stream(sk):
+            flushes[k % 2].zero_()
+            lo, n = shard.step_range(step_id, rank, world, B)
+            ev[k][0].record(sk)
+            g.run(n=n, first=lo, want_stats=False, stream=sk)
+            ev[k][1].record(sk)
         step_id += 1
+    for st_ in streams:
+        stream.wait_stream(st_)
+    t_end.record(stream)
     barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    kern_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    kern_s = t_start.elapsed_time(t_end) / 1e3
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
     stats = g.tally("stats").cpu().numpy()
     scat, cross, emitted = int(stats[4]), int(stats[5]), int(stats[0])
     t_max = shard.max_over_ranks(kern_s)
@@ -256,6 +277,7 @@ def main():
     traffic = traffic_from_profile()
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": achieved / peak_ops, "traffic": traffic,
+            "launch_ms_mean": sum(launch_ms) / len(launch_ms),
             "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                            f"{sm_max:.0f} MHz ({peak_kind} max SM clock)",
             "ops_per_scattering": OPS_PER_SCAT, "ops_per_crossing": OPS_PER_CROSS}
@@ -303,6 +325,7 @@ def main():
                        "T_K": 1e4, "source": "central point, line centre", "packets_per_step": B,
                        "job_packets": JOB_PACKETS, "scatterings_per_packet": scat_all / max(pk_all, 1),
                        "l2": "flushed before every timed step (256 MiB write)",
+                       "steps_issue": "two streams, alternating" if args.pipeline else "one stream",
                        "parallelism": f"packet-id shards x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": 2 * args.steps, "wall_s_timed": wall,

@@ -168,7 +168,9 @@ enum { KRL_PREC_FP32 = 0, KRL_PREC_FP64 = 1 };
 typedef struct {
     int precision;              /* KRL_PREC_FP32 (production) or KRL_PREC_FP64
                                    (same walk in double, for lockstep checks)       */
-    int block;                  /* threads per CTA (multiple of 32, <= 1024)        */
+    int block;                  /* threads per CTA, multiple of 32; at most 512 for
+                                   the FP32 walk without rich tallies (its default),
+                                   256 otherwise (the default there)               */
     int ctas_per_sm;            /* resident CTAs per SM of the persistent grid      */
     int refill_min;             /* a warp takes new packets once at least this many
                                    of its lanes are idle (1..32)                    */
@@ -197,6 +199,9 @@ typedef struct {
  * records[id - first_id]. stats (host, may be NULL): when given, the call
  * synchronises `s` and returns this run's counters, and returns
  * KRL_ERR_BUDGET if any packet exhausted max_iters. n = 0 is a no-op.
+ * Up to 8 runs of one grid may be in flight at once on different streams
+ * (each takes the next of 8 scratch slots in turn); tallies accumulate
+ * atomically, so their order does not matter beyond FP64 rounding.
  */
 KRL_API krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t seed,
                            const krl_tune* tune, krl_packet_record* records,

@@ -43,9 +43,11 @@ struct krl_grid {
     double* J = nullptr;
     float* emiss = nullptr;
     unsigned long long* stats = nullptr;      // cumulative [ST_N]
-    // scratch
-    unsigned long long* run_stats = nullptr;  // [ST_N] per run
-    unsigned long long* next = nullptr;       // work counter
+    // scratch: a ring of per-run slots so that runs on different streams can
+    // be in flight together (each slot: work counter + ST_N run counters)
+    unsigned long long* run_stats = nullptr;  // [kSlots][ST_N]
+    unsigned long long* next = nullptr;       // [kSlots] work counters
+    unsigned run_seq = 0;
     int* bad = nullptr;                       // validation flags
     double* scan_work = nullptr;
     size_t scan_work_n = 0;
@@ -113,6 +115,8 @@ void free_line(krl_grid* g)
     dfree(g->scan_work);
     g->line_ok = false;
 }
+
+constexpr int kSlots = 8;   // runs that may be in flight at once on one grid
 
 // Physical constants (CGS, CODATA 2018).
 constexpr double kKB = 1.380649e-16;
@@ -219,8 +223,8 @@ krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st
         if (src[k]) e = dalloc(&g->vel[k], n);
     if (e == cudaSuccess && d->n_coll) e = dalloc(&g->n_coll, n);
     if (e == cudaSuccess) e = dalloc(&g->stats, ST_N);
-    if (e == cudaSuccess) e = dalloc(&g->run_stats, ST_N);
-    if (e == cudaSuccess) e = dalloc(&g->next, 1);
+    if (e == cudaSuccess) e = dalloc(&g->run_stats, (size_t)kSlots * ST_N);
+    if (e == cudaSuccess) e = dalloc(&g->next, (size_t)kSlots);
     if (e == cudaSuccess) e = dalloc(&g->bad, 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->bad, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->opacity, d->opacity, n * 4, cudaMemcpyDeviceToDevice, s);
@@ -394,7 +398,7 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     cudaStream_t s = (cudaStream_t)st;
     if (!g) return fail(KRL_ERR_ARG, "krl_run_packets: NULL grid");
     if (!g->line_ok) return fail(KRL_ERR_STATE, "krl_run_packets before krl_line_set");
-    krl_tune T{KRL_PREC_FP32, 256, 0, 1, 1ull << 40};
+    krl_tune T{KRL_PREC_FP32, 512, 0, 1, 1ull << 40};
     if (tune) {
         if (tune->precision != KRL_PREC_FP32 && tune->precision != KRL_PREC_FP64)
             return fail(KRL_ERR_ARG, "unknown precision");
@@ -404,7 +408,7 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
         if (tune->refill_min) T.refill_min = tune->refill_min;
         if (tune->max_iters) T.max_iters = tune->max_iters;
     }
-    if (T.block < 32 || T.block > 256 || T.block % 32) return fail(KRL_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
+    if (T.block < 32 || T.block > 512 || T.block % 32) return fail(KRL_ERR_ARG, "block must be a multiple of 32 in [32, 512]");
     if (T.refill_min < 1 || T.refill_min > 32) return fail(KRL_ERR_ARG, "refill_min must be in [1, 32]");
     if (stats) memset(stats, 0, sizeof(*stats));
     if (n == 0) return KRL_OK;
@@ -417,6 +421,9 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     if (g->eps) rich |= kRichEps;
     if (rich) f |= F_RICH;
 
+    const int maxb = transport_max_block(T.precision, f);
+    if (!tune || !tune->block) T.block = maxb;
+    else if (T.block > maxb) return fail(KRL_ERR_ARG, "block %d exceeds %d for this walk", T.block, maxb);
     int occ = transport_occupancy(T.precision, f, T.block);
     if (occ < 1) return fail(KRL_ERR_CUDA, "transport kernel cannot be resident at block %d", T.block);
     int per_sm = T.ctas_per_sm > 0 ? (T.ctas_per_sm < occ ? T.ctas_per_sm : occ) : occ;
@@ -466,8 +473,11 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     A.exc = g->exc;
     A.J = g->J;
     A.emiss = g->emiss;
-    A.stats = g->run_stats;
-    A.next = g->next;
+    const int slot = (int)(g->run_seq++ % kSlots);
+    unsigned long long* slot_stats = g->run_stats + (size_t)slot * ST_N;
+    unsigned long long* slot_next = g->next + slot;
+    A.stats = slot_stats;
+    A.next = slot_next;
     A.rec = records;
     A.first = first_id;
     A.n = n;
@@ -476,13 +486,13 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     A.max_iters = T.max_iters;
     A.refill_min = T.refill_min;
 
-    KRL_CUDA(cudaMemsetAsync(g->next, 0, sizeof(unsigned long long), s), "reset work counter");
-    KRL_CUDA(cudaMemsetAsync(g->run_stats, 0, ST_N * sizeof(unsigned long long), s), "reset run counters");
+    KRL_CUDA(cudaMemsetAsync(slot_next, 0, sizeof(unsigned long long), s), "reset work counter");
+    KRL_CUDA(cudaMemsetAsync(slot_stats, 0, ST_N * sizeof(unsigned long long), s), "reset run counters");
     KRL_CUDA(launch_transport(A, T.precision, f, grid, T.block, s), "transport launch");
-    KRL_CUDA(add_counters(g->stats, g->run_stats, ST_N, s), "accumulate counters");
+    KRL_CUDA(add_counters(g->stats, slot_stats, ST_N, s), "accumulate counters");
     if (stats) {
         unsigned long long h[ST_N];
-        KRL_CUDA(cudaMemcpyAsync(h, g->run_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "read counters");
+        KRL_CUDA(cudaMemcpyAsync(h, slot_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "read counters");
         KRL_CUDA(cudaStreamSynchronize(s), "krl_run_packets");
         stats->emitted = h[ST_EMITTED];
         stats->escaped = h[ST_ESCAPED];

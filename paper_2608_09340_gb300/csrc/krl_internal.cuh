@@ -98,6 +98,8 @@ cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned fea
                              int grid, int block, cudaStream_t s);
 // Occupancy of one instantiation (CTAs per SM at this block size).
 int transport_occupancy(int precision, unsigned features, int block);
+// Largest CTA the instantiation is compiled for (512 lean FP32, else 256).
+int transport_max_block(int precision, unsigned features);
 
 // ---------------------------------------------------------------- setup kernels (tables.cu)
 struct LineTables {

@@ -51,10 +51,16 @@ __global__ void k_voigt(double a, const double* c, int N, double L, float* lnH, 
 // Mass of p(u | x) in the u-cell [lo, hi]: the Lorentz factor L(u) times
 // the second-order expansion of exp(-u^2) about the midpoint m, integrated
 // exactly: exp(-m^2) [I0 - 2 m I1 + (2 m^2 - 1) I2], Ik = int (u-m)^k L du.
+// u-node j = -6 + 0.048 j, rounded after the product and after the sum (no
+// fused multiply-add): the node at u = 0 must be exactly 0, because for a
+// tiny damping parameter a shift of 1e-16 moves the Lorentz spike of width a
+// across a cell edge.
+__device__ __forceinline__ double unode(int j) { return __dadd_rn(kUsU0, __dmul_rn(kUsDu, (double)j)); }
+
 __device__ double cell_mass(double x, double a, int j)
 {
-    double lo = kUsU0 + kUsDu * j;
-    double hi = kUsU0 + kUsDu * (j + 1);
+    double lo = unode(j);
+    double hi = unode(j + 1);
     double m = 0.5 * (lo + hi);
     double dl = lo - x, dh = hi - x;
     // Lorentz integral (atan(dh/a) - atan(dl/a)) / a; when the cell lies on
@@ -135,8 +141,8 @@ __global__ void k_rtable(const double* p, float* rtab)
     const double* row = p + (size_t)jx * (kUsNu - 1);
     double acc = 0.0;
     for (int c = 0; c < kUsNu - 1; ++c) {
-        double lo = kUsU0 + kUsDu * c;
-        double hi = kUsU0 + kUsDu * (c + 1);
+        double lo = unode(c);
+        double hi = unode(c + 1);
         double m = 0.5 * (lo + hi);
         double y = D - m * (g - 1.0);
         acc += row[c] * exp(-y * y * inv2s2);
@@ -252,7 +258,7 @@ __global__ void k_scan_finish(double* out, int n, const double* offs, int nb)
 __global__ void k_add_counters(unsigned long long* out, const unsigned long long* in, int n)
 {
     int i = threadIdx.x;
-    if (i < n) out[i] += in[i];
+    if (i < n && in[i]) atomicAdd(out + i, in[i]);   // runs on other streams may add too
 }
 
 }  // namespace

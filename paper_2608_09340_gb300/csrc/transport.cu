@@ -5,7 +5,8 @@
 // packet in registers. Whenever enough lanes of a warp are idle, the warp
 // takes a contiguous block of packet ids with ONE atomicAdd on a global work
 // counter (ballot + popc + shuffle) and the idle lanes emit those packets;
-// this is the server-worker scheme of Sec. 2.3.2 at warp granularity.
+// this is the server-worker scheme of Sec. 2.3.2 at warp granularity. After
+// the counter runs out, lanes finish their own packets independently.
 //
 // Per iteration a lane advances its packet by one event in the current
 // cell: with x_com = x_lab - n.V/b (Sec. 2.2.1) and alpha = alpha0
@@ -79,7 +80,8 @@ struct Ops<float> {
     static __device__ __forceinline__ float ln(float v) { return __logf(v); }
     static __device__ __forceinline__ float lg10(float v) { return __log2f(v) * 0.30102999566398120f; }
     static __device__ __forceinline__ float ex(float v) { return __expf(v); }
-    static __device__ __forceinline__ float sq(float v) { return sqrtf(v); }
+    // sqrt(v) for v >= 0 as v * rsqrt(v) (one MUFU op, 2 ulp)
+    static __device__ __forceinline__ float sq(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
     static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
     static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
     // sin and cos of 2 pi u for u in (0, 1): shift to [-pi, pi] where the
@@ -125,53 +127,81 @@ __device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
     return O::ex(((R)1 - f) * l0 + f * l1);
 }
 
-// Largest row i in [0, 38] with X[i] <= ax (closed-form guess, then fix-up).
+// Largest row i in [0, 38] with X[i] <= ax: closed-form guess from the node
+// formula, then one fix-up against the stored nodes (the guess is off by at
+// most one). Returns i and the two bracketing nodes.
 template <typename R>
-__device__ __forceinline__ int us_row(R ax, const float* sx)
+__device__ __forceinline__ int us_row2(R ax, const float* sx, R& x0, R& x1)
 {
     int i;
     if (ax < (R)8) i = (int)(ax * (R)2.25);
     else i = 18 + (int)((R)21 * Ops<R>::ln(ax * (R)0.125) * (R)0.27588297880498553);  // 1/ln(37.5)
     i = i < 0 ? 0 : (i > kUsNx - 2 ? kUsNx - 2 : i);
-    if (i > 0 && (R)sx[i] > ax) --i;
-    if (i > 0 && (R)sx[i] > ax) --i;
-    if (i < kUsNx - 2 && (R)sx[i + 1] <= ax) ++i;
-    if (i < kUsNx - 2 && (R)sx[i + 1] <= ax) ++i;
+    x0 = (R)sx[i];
+    x1 = (R)sx[i + 1];
+    while (i > 0 && x0 > ax) {
+        --i;
+        x1 = x0;
+        x0 = (R)sx[i];
+    }
+    while (i < kUsNx - 2 && x1 <= ax) {
+        ++i;
+        x0 = x1;
+        x1 = (R)sx[i + 1];
+    }
     return i;
 }
 
-// Invert one ln-CDF row at L = ln(xi): the largest node j in [0, 249] with
-// c[j] <= L, then linear interpolation of u between nodes j and j + 1. The
-// guide entry for logit(xi) gives a start at or next to j; the two bounded
-// walks make the result exactly the bisection's.
+// u_par for incoming gas-frame frequency x (|x| <= 300), given L = ln(xi)
+// and the guide bin m of logit(xi). Each bracketing row is inverted at L:
+// the largest node j with c[j] <= L (the guide entry starts at or next to
+// it; the bounded walks make the result exactly the bisection's), then u is
+// linear between nodes j and j + 1; the two rows' u are interpolated in |x|.
+// The two rows are walked together so their shared-memory loads overlap.
 template <typename R>
-__device__ __forceinline__ R us_invert(const float* row, const unsigned char* gd, int m, R L)
-{
-    int j = gd[m];
-    while (j > 0 && (R)row[j] > L) --j;
-    while (j < kUsNu - 2 && (R)row[j + 1] <= L) ++j;
-    R c0 = (R)row[j], c1 = (R)row[j + 1];
-    return (R)kUsU0 + (R)kUsDu * (R)j + (R)kUsDu * Ops<R>::dv(L - c0, c1 - c0);
-}
-
-// u_par for incoming gas-frame frequency x (|x| <= 300) from uniform xi.
-template <typename R>
-__device__ __forceinline__ R us_sample(R x, R xi, const float* sx, const float* sc, const unsigned char* sg)
+__device__ __forceinline__ R us_sample(R x, R L, int m, const float* sx, const float* sc, const unsigned char* sg)
 {
     using O = Ops<R>;
-    R ax = fabs(x);
-    int i = us_row(ax, sx);
-    R x0 = (R)sx[i], x1 = (R)sx[i + 1];
-    R t = O::dv(ax - x0, x1 - x0);
-    // L < 0 strictly (xi < 1), so node 250 (ln CDF = 0) always bounds the search
-    R L = fmin(O::ln(xi), (R)-1e-30);
-    R w = L - O::ln((R)1 - xi);
-    int m = (int)((w + (R)kGuideW) * (R)(kGuideN / (2.0 * kGuideW)));
-    m = m < 0 ? 0 : (m > kGuideN - 1 ? kGuideN - 1 : m);
-    R u0 = us_invert(sc + i * kUsNu, sg + i * kGuideN, m, L);
-    R u1 = us_invert(sc + (i + 1) * kUsNu, sg + (i + 1) * kGuideN, m, L);
-    R u = ((R)1 - t) * u0 + t * u1;
+    const R ax = fabs(x);
+    R x0, x1;
+    const int i = us_row2(ax, sx, x0, x1);
+    const R t = O::dv(ax - x0, x1 - x0);
+    const float* ra = sc + i * kUsNu;
+    const float* rb = ra + kUsNu;
+    int ja = sg[i * kGuideN + m];
+    int jb = sg[(i + 1) * kGuideN + m];
+    R a0 = (R)ra[ja], a1 = (R)ra[ja + 1];
+    R b0 = (R)rb[jb], b1 = (R)rb[jb + 1];
+    for (;;) {
+        const bool da = ja > 0 && a0 > L;
+        const bool db = jb > 0 && b0 > L;
+        if (!(da || db)) break;
+        if (da) { --ja; a1 = a0; a0 = (R)ra[ja]; }
+        if (db) { --jb; b1 = b0; b0 = (R)rb[jb]; }
+    }
+    for (;;) {
+        const bool ua = ja < kUsNu - 2 && a1 <= L;
+        const bool ub = jb < kUsNu - 2 && b1 <= L;
+        if (!(ua || ub)) break;
+        if (ua) { ++ja; a0 = a1; a1 = (R)ra[ja + 1]; }
+        if (ub) { ++jb; b0 = b1; b1 = (R)rb[jb + 1]; }
+    }
+    const R ua_ = (R)kUsU0 + (R)kUsDu * (R)ja + (R)kUsDu * O::dv(L - a0, a1 - a0);
+    const R ub_ = (R)kUsU0 + (R)kUsDu * (R)jb + (R)kUsDu * O::dv(L - b0, b1 - b0);
+    const R u = ((R)1 - t) * ua_ + t * ub_;
     return x < (R)0 ? -u : u;
+}
+
+// Guide bin of logit(xi) and L = ln(xi) (< 0 strictly: node 250, ln CDF = 0,
+// always bounds the search).
+template <typename R>
+__device__ __forceinline__ int us_bin(R xi, R& L)
+{
+    using O = Ops<R>;
+    L = fmin(O::ln(xi), (R)-1e-30);
+    const R w = L - O::ln((R)1 - xi);
+    int m = (int)((w + (R)kGuideW) * (R)(kGuideN / (2.0 * kGuideW)));
+    return m < 0 ? 0 : (m > kGuideN - 1 ? kGuideN - 1 : m);
 }
 
 // ---------------------------------------------------------------- packet state
@@ -188,7 +218,18 @@ struct Pkt {
     unsigned long long id;
     uint32_t vis_scat;     // scatterings in this cell visit
     R vis_exc;             // sum ds H over this cell visit
+    bool prev_scat;        // last event was a scattering (draw the next one early)
 };
+
+// n . V/b of a cell, always evaluated in this one fixed order (explicit
+// fused multiply-adds): the comoving frequency x_lab - n.V/b then recovers
+// exactly the value that x_lab was built from (e.g. 0 for line-centre
+// emission), whose sign the velocity sampler's symmetry depends on.
+template <typename R>
+__device__ __forceinline__ R vdot(R nx, R ny, R nz, const float4& rec)
+{
+    return fma(nz, (R)rec.w, fma(ny, (R)rec.z, nx * (R)rec.y));
+}
 
 template <typename R>
 __device__ __forceinline__ void set_dir(Pkt<R>& p, R nx, R ny, R nz)
@@ -324,6 +365,7 @@ __device__ bool emit(const TransportArgs& A, Pkt<R>& p)
     p.ncross = 0;
     p.vis_scat = 0;
     p.vis_exc = (R)0;
+    p.prev_scat = true;
     if (!inside) {
         p.x = xcom;
         p.cell0 = 0xFFFFFFFFu;
@@ -338,7 +380,7 @@ __device__ bool emit(const TransportArgs& A, Pkt<R>& p)
     p.c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
     p.cell0 = (uint32_t)p.c;
     p.rec = __ldg(A.cells + p.c);
-    R vdn = (F & F_VEL) ? p.nx * (R)p.rec.y + p.ny * (R)p.rec.z + p.nz * (R)p.rec.w : (R)0;
+    R vdn = (F & F_VEL) ? vdot<R>(p.nx, p.ny, p.nz, p.rec) : (R)0;
     p.x = xcom + vdn;
     return true;
 }
@@ -361,7 +403,7 @@ __device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xc
         const R cx = (R)A.cam[m][0], cy = (R)A.cam[m][1], cz = (R)A.cam[m][2];
         R g = p.nx * cx + p.ny * cy + p.nz * cz;
         g = fmin((R)1, fmax((R)-1, g));
-        R vc = (F & F_VEL) ? cx * (R)p.rec.y + cy * (R)p.rec.z + cz * (R)p.rec.w : (R)0;
+        R vc = (F & F_VEL) ? vdot<R>(cx, cy, cz, p.rec) : (R)0;
         // channels with |x_out,k - x_com| <= 10, x_out,k = -(x0 + (k + 1/2) dx) - vc
         R ctr = (-(R)A.ch_x0 - vc - xcom) / (R)A.ch_dx - (R)0.5;
         R span = (R)kRdMax / (R)A.ch_dx;
@@ -431,8 +473,14 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Launch shape per instantiation: the lean FP32 walk runs 512-thread CTAs,
+// two per SM (64 registers each); the FP64 and rich-tally walks need more
+// registers and run 256-thread CTAs.
 template <typename R, unsigned F>
-__global__ void __launch_bounds__(256) k_transport(const TransportArgs A)
+constexpr int max_block() { return (sizeof(R) == 4 && !(F & F_RICH)) ? 512 : 256; }
+
+template <typename R, unsigned F>
+__global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport(const TransportArgs A)
 {
     using O = Ops<R>;
     extern __shared__ float sm[];
@@ -450,12 +498,10 @@ __global__ void __launch_bounds__(256) k_transport(const TransportArgs A)
     const R a = (R)A.a;
     const R H0 = (R)__ldg(A.H0);
     const unsigned lane = threadIdx.x & 31u;
-    const int dims[3] = {A.nx, A.ny, A.nz};
-
     Pkt<R> p;
     bool active = false;
     bool exhausted = false;
-    unsigned long long st[ST_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long st_emit = 0, st_esc = 0, st_des = 0, st_stuck = 0, st_scat = 0, st_cross = 0;
 
     for (;;) {
         // ---- warp-level refill: one atomic per warp, ids compacted into idle lanes
@@ -471,35 +517,47 @@ __global__ void __launch_bounds__(256) k_transport(const TransportArgs A)
                     unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
                     if (k < A.n) {
                         p.id = A.first + k;
-                        ++st[ST_EMITTED];
+                        ++st_emit;
                         if (emit<R, F>(A, p)) {
                             active = true;
                         } else {
                             spectrum_add(A, (double)p.x);
-                            ++st[ST_ESCAPED];
+                            ++st_esc;
                             write_record(A, p, 1);
                         }
                     }
                 }
             }
         }
-        if (!__any_sync(kFull, active)) {
+        // Once the warp knows that no ids remain (a warp-uniform fact), idle
+        // lanes leave and active lanes finish their packets with no further
+        // warp-wide votes; until then every lane comes back to the ballot.
+        if (!active) {
             if (exhausted) break;
             continue;
         }
-        if (!active) continue;
 
         // ---- one event in the current cell
         if ((unsigned long long)p.nscat + p.ncross >= A.max_iters) {
             flush_visit<R, F>(A, p);
-            ++st[ST_STUCK];
-            st[ST_SCAT] += p.nscat;
-            st[ST_CROSS] += p.ncross;
+            ++st_stuck;
+            st_scat += p.nscat;
+            st_cross += p.ncross;
             write_record(A, p, 3);
             active = false;
             continue;
         }
-        const R vdn = (F & F_VEL) ? p.nx * (R)p.rec.y + p.ny * (R)p.rec.z + p.nz * (R)p.rec.w : (R)0;
+        // Draw the next scattering's random numbers before the profile lookup
+        // when the last event was a scattering (the common case deep in the
+        // line core): the two Philox chains overlap the lookup's latency.
+        const uint32_t idlo = (uint32_t)p.id, idhi = (uint32_t)(p.id >> 32);
+        Words w0 = {{0u, 0u, 0u, 0u}}, w1 = {{0u, 0u, 0u, 0u}};
+        const bool spec = p.prev_scat;
+        if (spec) {
+            w0 = philox(idlo, idhi, p.nscat + 1u, 0u, A.k0, A.k1);
+            w1 = philox(idlo, idhi, p.nscat + 1u, 1u, A.k0, A.k1);
+        }
+        const R vdn = (F & F_VEL) ? vdot<R>(p.nx, p.ny, p.nz, p.rec) : (R)0;
         const R xcom = p.x - vdn;
         const R H = voigt<R>(xcom, sv, a, H0);
         const R alpha = (R)p.rec.x * H;
@@ -520,83 +578,96 @@ __global__ void __launch_bounds__(256) k_transport(const TransportArgs A)
             if (A.rich & KRL_TALLY_EXC) p.vis_exc += ds * H;
             if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H);
         }
+        p.prev_scat = scat;
         if (scat) {
             // ---- scattering (event e = nscat): block 0 = {u_par, bm_r, bm_phi, tau},
             //      block 1 = {mu, phi, eps_test, -}
             ++p.nscat;
             ++p.vis_scat;
-            const uint32_t lo = (uint32_t)p.id, hi = (uint32_t)(p.id >> 32);
-            Words w0 = philox(lo, hi, p.nscat, 0u, A.k0, A.k1);
-            Words w1 = philox(lo, hi, p.nscat, 1u, A.k0, A.k1);
+            if (!spec) {
+                w0 = philox(idlo, idhi, p.nscat, 0u, A.k0, A.k1);
+                w1 = philox(idlo, idhi, p.nscat, 1u, A.k0, A.k1);
+            }
             if ((F & F_RICH) && (A.rich & kRichEps)) {
                 if (O::uni(w1.w[2]) < (R)__ldg(A.eps + p.c)) {
                     flush_visit<R, F>(A, p);
-                    ++st[ST_DESTROYED];
-                    st[ST_SCAT] += p.nscat;
-                    st[ST_CROSS] += p.ncross;
+                    ++st_des;
+                    st_scat += p.nscat;
+                    st_cross += p.ncross;
                     write_record(A, p, 2);
                     active = false;
                     continue;
                 }
             }
+            // independent long-latency work first: Box-Muller, new direction,
+            // the sampler's logs; then the table walk
             R bs, bc;
             O::sc2pi(O::uni(w0.w[2]), &bs, &bc);
             const R rad = O::sq(fmax((R)0, -O::ln(O::uni(w0.w[1]))));
-            const R z1 = rad * bc, z2 = rad * bs;
-            const R upar = fabs(xcom) > (R)300 ? z2 : us_sample<R>(xcom, O::uni(w0.w[0]), sx, sc, sg);
             R mx, my, mz;
             iso_dir<R>(O::uni(w1.w[0]), O::uni(w1.w[1]), mx, my, mz);
+            R L;
+            const int gm = us_bin<R>(O::uni(w0.w[0]), L);
+            const R tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
+            const R z1 = rad * bc, z2 = rad * bs;
+            const R upar = fabs(xcom) > (R)300 ? z2 : us_sample<R>(xcom, L, gm, sx, sc, sg);
             const R g = p.nx * mx + p.ny * my + p.nz * mz;
-            const R sg = O::sq(fmax((R)0, (R)1 - g * g));
-            const R xout = xcom + upar * (g - (R)1) + z1 * sg;
+            const R sg_ = O::sq(fmax((R)0, (R)1 - g * g));
+            const R xout = xcom + upar * (g - (R)1) + z1 * sg_;
             set_dir(p, mx, my, mz);
-            const R vdo = (F & F_VEL) ? mx * (R)p.rec.y + my * (R)p.rec.z + mz * (R)p.rec.w : (R)0;
+            const R vdo = (F & F_VEL) ? vdot<R>(mx, my, mz, p.rec) : (R)0;
             p.x = xout + vdo;
-            p.tau = fmax((R)0, -O::ln(O::uni(w0.w[3])));
+            p.tau = tau_new;
         } else {
             // ---- cross the face on `axis`
             p.tau -= alpha * sx_;
             ++p.ncross;
             flush_visit<R, F>(A, p);
-            int ci[3] = {p.cx, p.cy, p.cz};
-            R nd = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
-            int step = nd > (R)0 ? 1 : -1;
-            int nc = ci[axis] + step;
-            R pnew = step > 0 ? (R)0 : (R)1;
+            const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
+            const int stride = axis == 0 ? 1 : (axis == 1 ? A.nx : A.nx * A.ny);
+            const int cur = axis == 0 ? p.cx : (axis == 1 ? p.cy : p.cz);
+            const R nd = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+            const int step = nd > (R)0 ? 1 : -1;
+            int nc = cur + step;
+            int dc = step * stride;
+            const R pnew = step > 0 ? (R)0 : (R)1;
             if (axis == 0) p.px = pnew;
             else if (axis == 1) p.py = pnew;
             else p.pz = pnew;
-            if (nc < 0 || nc >= dims[axis]) {
+            if (nc < 0 || nc >= dim) {
                 if (!((A.periodic >> axis) & 1u)) {
                     spectrum_add(A, (double)p.x);
-                    ++st[ST_ESCAPED];
-                    st[ST_SCAT] += p.nscat;
-                    st[ST_CROSS] += p.ncross;
+                    ++st_esc;
+                    st_scat += p.nscat;
+                    st_cross += p.ncross;
                     write_record(A, p, 1);
                     active = false;
                     continue;
                 }
-                nc = nc < 0 ? nc + dims[axis] : nc - dims[axis];
+                if (nc < 0) { nc += dim; dc += dim * stride; }
+                else { nc -= dim; dc -= dim * stride; }
             }
-            ci[axis] = nc;
-            p.cx = ci[0];
-            p.cy = ci[1];
-            p.cz = ci[2];
-            p.c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
+            if (axis == 0) p.cx = nc;
+            else if (axis == 1) p.cy = nc;
+            else p.cz = nc;
+            p.c += dc;
             p.rec = __ldg(A.cells + p.c);
         }
     }
 
+    const unsigned long long tot[6] = {warp_sum(st_emit), warp_sum(st_esc), warp_sum(st_des),
+                                       warp_sum(st_stuck), warp_sum(st_scat), warp_sum(st_cross)};
+    if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < ST_N; ++k) {
-        unsigned long long v = warp_sum(st[k]);
-        if (lane == 0 && v) atomicAdd(A.stats + k, v);
+        for (int k = 0; k < 6; ++k)
+            if (tot[k]) atomicAdd(A.stats + k, tot[k]);
     }
 }
 
 template <typename R, unsigned F>
 cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t s)
 {
+    if (block > max_block<R, F>()) return cudaErrorInvalidConfiguration;
     auto kern = k_transport<R, F>;
     static bool configured = false;   // per instantiation, per process
     if (!configured) {
@@ -611,6 +682,7 @@ cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t
 template <typename R, unsigned F>
 int occupancy_one(int block)
 {
+    if (block > max_block<R, F>()) return 0;
     auto kern = k_transport<R, F>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     int n = 0;
@@ -655,6 +727,11 @@ cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned fea
 {
     return precision == KRL_PREC_FP64 ? dispatch<double>(A, features, grid, block, s)
                                       : dispatch<float>(A, features, grid, block, s);
+}
+
+int transport_max_block(int precision, unsigned features)
+{
+    return (precision == KRL_PREC_FP32 && !(features & F_RICH)) ? 512 : 256;
 }
 
 int transport_occupancy(int precision, unsigned features, int block)

@@ -14,6 +14,13 @@
 //    sum_k (2k-1)!! / (2 z^2)^k, summed until the terms stop shrinking. Its
 //    real part is formed without cancellation, which keeps H accurate deep
 //    in the Lorentz wing where Re w << |w|.
+//  * a < 1e-6 and |x| < 8: the expansion of Re w(x + i a) in powers of a
+//    (Taylor series of w about the real axis, w' = -2 z w + 2 i / sqrt(pi)):
+//      H = exp(-x^2) + (2a/sqrt(pi)) (2 x D(x) - 1) + a^2 (1 - 2x^2) exp(-x^2),
+//    D the Dawson function; the rational expansion's absolute error
+//    (~1e-16 |w|) would swamp H there, which falls to ~1e-15 near |x| = 6.
+//    D(x) = exp(-x^2) sum_n x^(2n+1) / (n! (2n+1)), a series of positive
+//    terms (no cancellation).
 #pragma once
 
 #include <cmath>
@@ -101,11 +108,31 @@ KRL_HD inline double faddeeva_asymptotic_re(double x, double y)
     return rsqrtpi * w.re;
 }
 
+// Dawson's function for 0 <= x < 8 by the erfi power series.
+KRL_HD inline double dawson(double x)
+{
+    const double x2 = x * x;
+    double term = x;              // x^(2n+1) / n!
+    double sum = x;
+    for (int n = 1; n < 400; ++n) {
+        term *= x2 / n;
+        double add = term / (2 * n + 1);
+        sum += add;
+        if (add < 1e-17 * sum) break;
+    }
+    return std::exp(-x2) * sum;
+}
+
 // H(a, x) for a > 0.
 KRL_HD inline double voigt_H(double a, double x, const double* c, int N, double L)
 {
     double ax = std::fabs(x);
     if (ax >= 8.0) return faddeeva_asymptotic_re(ax, a);
+    if (a < 1e-6) {
+        const double e = std::exp(-ax * ax);
+        const double rsqrtpi2 = 1.1283791670955125739;   // 2 / sqrt(pi)
+        return e + a * rsqrtpi2 * (2.0 * ax * dawson(ax) - 1.0) + a * a * (1.0 - 2.0 * ax * ax) * e;
+    }
     return faddeeva_rational(ax, a, c, N, L).re;
 }
 

@@ -70,8 +70,10 @@ def test_lockstep(name):
                                atol=1e-12 * max(1.0, ref["J"].max()))
         if ref["emiss"] is not None:
             e, re_ = gpu["emiss"].reshape(ref["emiss"].shape), ref["emiss"]
-            # FP32 accumulation on the device (the method keeps the cube in FP32)
-            assert np.allclose(e, re_, rtol=2e-5, atol=1e-6 * re_.max())
+            # The device accumulates the cube in FP32 (the method keeps it in single
+            # precision) with atomics in no fixed order; a cell-channel sum of N
+            # terms then carries up to ~N 2^-24 relative rounding (N ~ 1e4 here).
+            assert np.allclose(e, re_, rtol=1e-3, atol=1e-6 * re_.max())
 
 
 def test_edge_cases():

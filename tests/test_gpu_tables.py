@@ -12,7 +12,7 @@ from _gpu_common import need_gpu
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("a", [1e-2, 4.7e-4, 0.149, 1e-4])
+@pytest.mark.parametrize("a", [1e-2, 4.7e-4, 0.149, 1e-4, 1.55e-13])
 def test_tables_match_oracle(a):
     krl = need_gpu()
     p = W.thin_slab()

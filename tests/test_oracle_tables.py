@@ -259,3 +259,16 @@ def test_python_and_c_kernel_lookup_agree(oracle_mod):
     for _ in range(300):
         D, x, g = rng.uniform(-11, 11), rng.uniform(-130, 130), rng.uniform(-1, 1)
         assert abs(T.r_lookup(D, x, g, tb["rtab"]) - L.rkernel(D, x, g)) < 1e-12
+
+
+def test_voigt_tiny_damping_against_arbitrary_precision():
+    """The envelope workload's line has a ~ 1.6e-13, where H falls to ~1e-15
+    near |x| = 6: the oracle's Faddeeva values keep their relative accuracy
+    (checked against a 50-digit evaluation of Re[exp(-z^2) erfc(-iz)])."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    a = 1.5505323925448215e-13
+    for x in (0.0, 2.0, 5.0, 5.6, 6.0, 6.5, 7.0, 7.9, 12.0):
+        z = mp.mpc(x, a)
+        ref = float(mp.re(mp.exp(-z * z) * mp.erfc(-1j * z)))
+        assert abs(T.voigt_H(a, x) / ref - 1) < 1e-12
