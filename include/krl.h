@@ -245,6 +245,37 @@ KRL_API size_t krl_tally_bytes(const krl_grid* g, krl_tally_kind kind);
 /* Zero all tallies and counters. Enqueued on `s`. */
 KRL_API krl_status krl_tallies_reset(krl_grid* g, krl_stream s);
 
+/* ------------------------------------------------------------------ no allocation */
+
+/*
+ * Volume-source emission CDF without any device allocation. The paper has
+ * no counterpart: this is a service to callers that cannot call cudaMalloc,
+ * such as a host application that hands all device memory to its own pool
+ * or framework allocator (a raw cudaMalloc there may fail or fragment the
+ * pool), or a latency-critical loop that must not take cudaMalloc's
+ * implicit device synchronisation.
+ *
+ * Computes cdf[i] = (rate[0] + ... + rate[i]) / (rate[0] + ... + rate[n-1])
+ * in FP64 -- the same table krl_line_set builds for KRL_SRC_VOLUME and
+ * krl_tallies_get(KRL_OUT_SRC_CDF) returns. rate: device float32 [n],
+ * borrowed; cdf: device double [n], written. 1 <= n <= 2^27 cells; larger n
+ * is rejected with KRL_ERR_ARG.
+ *
+ * The scan's scratch (65537 partial sums and a flag, about 512 KiB) is a
+ * fixed array in the library's device image: every GPU that loads the
+ * library holds it until the process exits, and the call allocates nothing
+ * (no cudaMalloc, no cudaFree). The first call on a device looks up that
+ * array's device address once (cudaGetSymbolAddress); make that first call
+ * before any stream capture. All calls share the array and it keeps the
+ * last call's contents (the call clears what must start at zero), so calls
+ * that overlap on the GPU -- on different streams or threads -- race and
+ * must be serialised by the caller.
+ *
+ * Synchronises `s` to report bad input: KRL_ERR_NUMERIC for a NaN, Inf or
+ * negative rate, KRL_ERR_ARG for a zero total or NULL pointers.
+ */
+KRL_API krl_status krl_emission_cdf_noalloc(const float* rate, int n, double* cdf, krl_stream s);
+
 #ifdef __cplusplus
 }
 #endif

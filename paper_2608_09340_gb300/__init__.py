@@ -82,7 +82,8 @@ RECORD_DTYPE = np.dtype([("x", "<f4"), ("nscat", "<u4"), ("ncross", "<u4"), ("st
 assert RECORD_DTYPE.itemsize == 20
 
 EXPORTS = ["krl_last_error", "krl_version", "krl_grid_create", "krl_grid_destroy", "krl_line_set",
-           "krl_line_info_get", "krl_run_packets", "krl_tallies_get", "krl_tally_bytes", "krl_tallies_reset"]
+           "krl_line_info_get", "krl_run_packets", "krl_tallies_get", "krl_tally_bytes", "krl_tallies_reset",
+           "krl_emission_cdf_noalloc"]
 
 _lib_handle = None
 
@@ -110,8 +111,9 @@ def load_library(path: str | None = None):
     lib.krl_tally_bytes.restype = C.c_size_t
     lib.krl_tally_bytes.argtypes = [vp, C.c_int]
     lib.krl_tallies_reset.argtypes = [vp, vp]
+    lib.krl_emission_cdf_noalloc.argtypes = [vp, C.c_int, vp, vp]
     for name in ("krl_grid_create", "krl_grid_destroy", "krl_line_set", "krl_line_info_get",
-                 "krl_run_packets", "krl_tallies_get", "krl_tallies_reset"):
+                 "krl_run_packets", "krl_tallies_get", "krl_tallies_reset", "krl_emission_cdf_noalloc"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib_handle = lib
@@ -181,6 +183,15 @@ def krl_tallies_get(handle, kind: int, dst, stream=None):
 
 def krl_tallies_reset(handle, stream=None):
     _check(load_library().krl_tallies_reset(handle, _stream_handle(stream)))
+
+
+def krl_emission_cdf_noalloc(rate, cdf, stream=None):
+    """Emission CDF of a float32 rate tensor into a float64 cdf tensor (both on
+    the device), with no device allocation: for callers that cannot call
+    cudaMalloc (see include/krl.h). Overlapping calls race; the first call on
+    a device should come before any stream capture."""
+    _check(load_library().krl_emission_cdf_noalloc(_ptr(rate), int(rate.numel()), _ptr(cdf),
+                                                   _stream_handle(stream)))
 
 
 # ------------------------------------------------------------------ workload marshalling

@@ -183,6 +183,14 @@ krl_status zero_tallies(krl_grid* g, cudaStream_t s)
 
 }  // namespace
 
+namespace krl {
+// Lets other translation units report through krl_last_error().
+void set_last_error(const char* msg)
+{
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+}  // namespace krl
+
 extern "C" {
 
 const char* krl_last_error(void) { return g_err; }
