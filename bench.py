@@ -53,6 +53,7 @@ def parse():
                     help="centre-to-edge line-centre depth (1e6 is the benchmark; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-raytrace", action="store_true")
     ap.add_argument("--serial", dest="pipeline", action="store_false",
                     help="issue every step on one stream (no overlap of one step's tail with the next)")
     return ap.parse_args()
@@ -137,6 +138,48 @@ def traffic_from_profile():
         return float(vals["dram_bytes_per_launch_scaled"].strip())
     except Exception:
         return None
+
+
+RT_GRID = 256
+RT_CHANNELS = 64
+RT_PIXELS = 1024
+RT_CAMERAS = 3
+
+
+def bench_raytrace(args, dev):
+    """Channel maps of the config-5 image: a 256^3 rotating, infalling
+    envelope with 64 velocity channels over +-5 km/s, imaged at 1024^2 pixels
+    from 3 inclinations (0, 45, 90 deg). The emissivity cube (3 x 256^3 x 64
+    FP32) is filled by a Monte Carlo pass of 1e6 packets first; one pass =
+    the three cameras' ray traces, timed with CUDA events."""
+    import torch
+    import paper_2608_09340_gb300 as krl
+    import workloads as W
+    p = W.envelope(n=RT_GRID, n_ch=RT_CHANNELS, n_packets=1_000_000)
+    g = krl.Grid(p, device=dev)
+    try:
+        g.run(want_stats=False)
+        for _ in range(max(1, args.warmup)):
+            for m in range(RT_CAMERAS):
+                g.raytrace(m, RT_PIXELS, RT_PIXELS, fov_cells=float(RT_GRID))
+        torch.cuda.synchronize(dev)
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, args.steps)
+        e0.record(stream)
+        for _ in range(reps):
+            for m in range(RT_CAMERAS):
+                g.raytrace(m, RT_PIXELS, RT_PIXELS, fov_cells=float(RT_GRID))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+    finally:
+        g.close()
+    rays = RT_CAMERAS * RT_PIXELS * RT_PIXELS
+    return {"workload": f"envelope {RT_GRID}^3, {RT_CHANNELS} ch, {RT_PIXELS}^2 px, {RT_CAMERAS} inclinations",
+            "rays_per_s": rays / ms * 1e3, "channel_rays_per_s": rays * RT_CHANNELS / ms * 1e3,
+            "ms_per_pass": ms, "passes": reps, "gpu_launches_per_pass": RT_CAMERAS,
+            "emissivity_bytes": RT_CAMERAS * RT_GRID ** 3 * RT_CHANNELS * 4}
 
 
 def run_reference(args, rank):
@@ -314,6 +357,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p)
     g.close()
+    rt = None
+    if rank == 0 and not args.no_raytrace:
+        rt = bench_raytrace(args, dev)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -327,7 +373,7 @@ def main():
                        "l2": "flushed before every timed step (256 MiB write)",
                        "steps_issue": "two streams, alternating" if args.pipeline else "one stream",
                        "parallelism": f"packet-id shards x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "raytrace": rt,
             "gpu_launches": 2 * args.steps, "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

@@ -245,6 +245,35 @@ KRL_API size_t krl_tally_bytes(const krl_grid* g, krl_tally_kind kind);
 /* Zero all tallies and counters. Enqueued on `s`. */
 KRL_API krl_status krl_tallies_reset(krl_grid* g, krl_stream s);
 
+/* ------------------------------------------------------------------ channel maps */
+
+typedef struct {
+    int camera;             /* >= 0: the line's camera `camera` (direction from
+                               cam_theta/cam_phi; emissivity defaults to this
+                               grid's tally for it); -1: use theta/phi below    */
+    double theta, phi;      /* camera direction when camera == -1              */
+    int npix_x, npix_y;     /* pixels, >= 1                                     */
+    double fov_cells;       /* image width in cell units (square pixels)       */
+    const float* emiss;     /* device [ncell][n_ch] camera-directed scattering
+                               emissivity (raw KRL_OUT_EMISS units), or NULL for
+                               this grid's tally of `camera`                    */
+    const float* jline;     /* device [ncell] frequency-integrated line emission
+                               per unit path (same units), or NULL              */
+} krl_raytrace_desc;
+
+/*
+ * Deterministic ray trace of channel maps (Sec. 2.2.2, Eq. imaging-formal,
+ * Eq. imaging-alphas): orthographic, pixel-centred parallel rays along the
+ * camera direction n, image axes (e_theta, e_phi), centred on the box, no
+ * incoming intensity; per cell segment dl and channel k (the line's
+ * v_k = v_min + (k + 1/2) dv, 1 <= n_ch <= 128) with x_k = -(v_k + n.V)/b:
+ * I <- I e^{-dtau} + j_k dl (1 - e^{-dtau})/dtau, dtau = alpha0 H(a, x_k) dl,
+ * j_k = emiss_k + jline H(a, x_k)/sqrt(pi). maps: device float32
+ * [n_ch][npix_y][npix_x], written (raw units: emissivity x cell widths).
+ * All faces are open for the rays. Enqueued on `s`; does not synchronise.
+ */
+KRL_API krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float* maps, krl_stream s);
+
 /* ------------------------------------------------------------------ no allocation */
 
 /*

@@ -67,6 +67,11 @@ class krl_line_info(C.Structure):
                 ("sigma0_cm2", C.c_double), ("H0", C.c_double), ("ncell", C.c_int)]
 
 
+class krl_raytrace_desc(C.Structure):
+    _fields_ = [("camera", C.c_int), ("theta", C.c_double), ("phi", C.c_double), ("npix_x", C.c_int),
+                ("npix_y", C.c_int), ("fov_cells", C.c_double), ("emiss", C.c_void_p), ("jline", C.c_void_p)]
+
+
 class krl_tune(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("ctas_per_sm", C.c_int),
                 ("refill_min", C.c_int), ("max_iters", C.c_uint64)]
@@ -83,7 +88,7 @@ assert RECORD_DTYPE.itemsize == 20
 
 EXPORTS = ["krl_last_error", "krl_version", "krl_grid_create", "krl_grid_destroy", "krl_line_set",
            "krl_line_info_get", "krl_run_packets", "krl_tallies_get", "krl_tally_bytes", "krl_tallies_reset",
-           "krl_emission_cdf_noalloc"]
+           "krl_emission_cdf_noalloc", "krl_raytrace_channels"]
 
 _lib_handle = None
 
@@ -112,8 +117,10 @@ def load_library(path: str | None = None):
     lib.krl_tally_bytes.argtypes = [vp, C.c_int]
     lib.krl_tallies_reset.argtypes = [vp, vp]
     lib.krl_emission_cdf_noalloc.argtypes = [vp, C.c_int, vp, vp]
+    lib.krl_raytrace_channels.argtypes = [vp, C.POINTER(krl_raytrace_desc), vp, vp]
     for name in ("krl_grid_create", "krl_grid_destroy", "krl_line_set", "krl_line_info_get",
-                 "krl_run_packets", "krl_tallies_get", "krl_tallies_reset", "krl_emission_cdf_noalloc"):
+                 "krl_run_packets", "krl_tallies_get", "krl_tallies_reset", "krl_emission_cdf_noalloc",
+                 "krl_raytrace_channels"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib_handle = lib
@@ -183,6 +190,10 @@ def krl_tallies_get(handle, kind: int, dst, stream=None):
 
 def krl_tallies_reset(handle, stream=None):
     _check(load_library().krl_tallies_reset(handle, _stream_handle(stream)))
+
+
+def krl_raytrace_channels(handle, desc: krl_raytrace_desc, maps, stream=None):
+    _check(load_library().krl_raytrace_channels(handle, C.byref(desc), _ptr(maps), _stream_handle(stream)))
 
 
 def krl_emission_cdf_noalloc(rate, cdf, stream=None):
@@ -297,6 +308,18 @@ class Grid:
 
     def reset(self, stream=None):
         krl_tallies_reset(self.handle, stream)
+
+    def raytrace(self, camera: int, npix_x: int, npix_y: int, fov_cells: float, emiss=None, jline=None,
+                 theta: float = 0.0, phi: float = 0.0, stream=None):
+        """Channel maps [n_ch, npix_y, npix_x] (float32 tensor) for one camera."""
+        import torch
+        nch = self.problem.channels[2]
+        maps = torch.empty((nch, npix_y, npix_x), dtype=torch.float32, device=self.device)
+        d = krl_raytrace_desc(camera, theta, phi, npix_x, npix_y, fov_cells,
+                              emiss.data_ptr() if emiss is not None else None,
+                              jline.data_ptr() if jline is not None else None)
+        krl_raytrace_channels(self.handle, d, maps, stream)
+        return maps
 
 
 def records_to_numpy(rec_tensor) -> np.ndarray:

@@ -303,7 +303,8 @@ krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
     free_line(g);
     KRL_CUDA(cudaMemsetAsync(g->bad, 0, sizeof(int), s), "krl_line_set");
     krl_line_desc L = *d;
-    if (!need_ch) L.n_ch = 0;
+    // keep a channel grid for the ray trace even without J / emissivity tallies
+    if (!need_ch && !(d->n_ch >= 1 && d->ch_dv_cms > 0)) L.n_ch = 0;
     if (!(L.tally_flags & KRL_TALLY_EMISS)) L.n_cam = 0;
     g->line = L;
 
@@ -510,6 +511,65 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
         stats->crossings = h[ST_CROSS];
         if (h[ST_STUCK]) return fail(KRL_ERR_BUDGET, "%llu packets exhausted max_iters", h[ST_STUCK]);
     }
+    return KRL_OK;
+}
+
+krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float* maps, krl_stream st)
+{
+    if (!g || !d || !maps) return fail(KRL_ERR_ARG, "krl_raytrace_channels: NULL argument");
+    if (!g->line_ok) return fail(KRL_ERR_STATE, "krl_raytrace_channels before krl_line_set");
+    const krl_line_desc& L = g->line;
+    if (L.n_ch < 1 || L.n_ch > 128) return fail(KRL_ERR_ARG, "ray trace needs 1..128 line channels (line has %d)", L.n_ch);
+    if (d->npix_x < 1 || d->npix_y < 1 || !(d->fov_cells > 0) || !isfinite(d->fov_cells))
+        return fail(KRL_ERR_ARG, "bad image size");
+    double th, ph;
+    const float* em = d->emiss;
+    if (d->camera >= 0) {
+        if (d->camera >= L.n_cam) return fail(KRL_ERR_ARG, "camera %d not defined (line has %d)", d->camera, L.n_cam);
+        th = L.cam_theta[d->camera];
+        ph = L.cam_phi[d->camera];
+        if (!em) {
+            if (!g->emiss) return fail(KRL_ERR_STATE, "no emissivity tally on this grid");
+            em = g->emiss + (size_t)d->camera * g->ncell * L.n_ch;
+        }
+    } else if (d->camera == -1) {
+        th = d->theta;
+        ph = d->phi;
+        if (!em) return fail(KRL_ERR_ARG, "camera -1 needs an emissivity buffer");
+        if (!isfinite(th) || !isfinite(ph)) return fail(KRL_ERR_ARG, "bad camera angles");
+    } else {
+        return fail(KRL_ERR_ARG, "camera must be >= -1");
+    }
+    RayArgs A{};
+    A.cells = g->cells;
+    A.nx = g->nx;
+    A.ny = g->ny;
+    A.nz = g->nz;
+    A.voigt_lnH = g->tab.voigt_lnH;
+    A.H0 = g->tab.H0;
+    A.a = (float)g->info.a;
+    A.emiss = em;
+    A.jline = d->jline;
+    A.n_ch = L.n_ch;
+    A.ch_x0 = L.ch_vmin_cms / g->info.b_cms;
+    A.ch_dx = L.ch_dv_cms / g->info.b_cms;
+    A.n[0] = sin(th) * cos(ph);
+    A.n[1] = sin(th) * sin(ph);
+    A.n[2] = cos(th);
+    A.u[0] = cos(th) * cos(ph);
+    A.u[1] = cos(th) * sin(ph);
+    A.u[2] = -sin(th);
+    A.v[0] = -sin(ph);
+    A.v[1] = cos(ph);
+    A.v[2] = 0.0;
+    A.centre[0] = 0.5 * g->nx;
+    A.centre[1] = 0.5 * g->ny;
+    A.centre[2] = 0.5 * g->nz;
+    A.pix = d->fov_cells / d->npix_x;
+    A.npix_x = d->npix_x;
+    A.npix_y = d->npix_y;
+    A.maps = maps;
+    KRL_CUDA(launch_raytrace(A, (cudaStream_t)st), "ray trace launch");
     return KRL_OK;
 }
 

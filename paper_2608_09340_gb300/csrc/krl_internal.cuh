@@ -101,6 +101,25 @@ int transport_occupancy(int precision, unsigned features, int block);
 // Largest CTA the instantiation is compiled for (512 lean FP32, else 256).
 int transport_max_block(int precision, unsigned features);
 
+// ---------------------------------------------------------------- ray trace (raytrace.cu)
+struct RayArgs {
+    const float4* cells;      // per-cell record (alpha0 dx, V/b)
+    int nx, ny, nz;
+    const float* voigt_lnH;
+    const float* H0;
+    float a;
+    const float* emiss;       // [ncell][n_ch] camera-directed scattering emissivity
+    const float* jline;       // [ncell] frequency-integrated line emission, or nullptr
+    int n_ch;
+    double ch_x0, ch_dx;      // v_min / b, dv / b
+    double n[3], u[3], v[3];  // camera direction and image axes
+    double centre[3];         // image centre (box centre), cell units
+    double pix;               // pixel size, cell units
+    int npix_x, npix_y;
+    float* maps;              // [n_ch][npix_y][npix_x]
+};
+cudaError_t launch_raytrace(const RayArgs& A, cudaStream_t s);
+
 // ---------------------------------------------------------------- setup kernels (tables.cu)
 struct LineTables {
     float* voigt_lnH;   // [kVoigtN]

@@ -1,0 +1,74 @@
+"""GPU channel-map ray trace against the FP64 oracle trace on the same
+emissivity (criterion: max |I - I_ref| / max(|I_ref|, 1e-3 max I_ref) <= 1e-5),
+and the full two-step chain on the thin moving slab (Eq. thin-slab)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import raytrace as RT
+from _gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _crit(got, ref):
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    return np.max(np.abs(np.asarray(got, dtype=np.float64) - ref) / den)
+
+
+def test_raytrace_matches_fp64_on_the_mc_emissivity():
+    krl = need_gpu()
+    import torch
+    p = W.envelope(n=16, n_ch=16, n_packets=20000)
+    g = krl.Grid(p)
+    try:
+        g.run(precision=krl.KRL_PREC_FP32, want_stats=False)
+        em = g.tally("emiss").reshape(len(p.cameras), p.ncell, p.channels[2])
+        jline = torch.from_numpy((1e-3 * p.source.rate.reshape(-1)).astype(np.float32)).cuda()
+        for m in range(len(p.cameras)):
+            for jl in (None, jline):
+                maps = g.raytrace(m, 24, 20, fov_cells=17.0, jline=jl).cpu().numpy()
+                ref = RT.trace_maps(oracle, p, em[m].cpu().numpy(), camera=m, npix_x=24, npix_y=20, fov=17.0,
+                                    jline=None if jl is None else jl.cpu().numpy())
+                assert np.abs(ref).max() > 0
+                assert _crit(maps, ref) <= 1e-5, (m, jl is None, _crit(maps, ref))
+        # an explicit direction with a caller emissivity buffer
+        th, ph = math.radians(30.0), math.radians(70.0)
+        maps = g.raytrace(-1, 9, 11, fov_cells=20.0, emiss=em[0].contiguous(), theta=th, phi=ph).cpu().numpy()
+        q = W.envelope(n=16, n_ch=16, n_packets=1)
+        q.cameras = ((th, ph),)
+        ref = RT.trace_maps(oracle, q, em[0].cpu().numpy(), camera=0, npix_x=9, npix_y=11, fov=20.0)
+        assert _crit(maps, ref) <= 1e-5
+    finally:
+        g.close()
+
+
+def test_thin_slab_two_step_chain():
+    """MC emissivity + ray trace through the face-on camera: the image carries
+    the volume-integrated emissivity (thin slab), peaked at v = -v_z with the
+    thermal shape of Eq. thin-slab."""
+    krl = need_gpu()
+    p = W.thin_slab(n_packets=200000)
+    g = krl.Grid(p)
+    try:
+        g.run(precision=krl.KRL_PREC_FP32, want_stats=False)
+        em = g.tally("emiss").cpu().numpy().reshape(p.ncell, -1).astype(np.float64)
+        npx = 32
+        fov = float(p.shape[2])
+        maps = g.raytrace(0, npx, npx, fov_cells=fov).cpu().numpy().astype(np.float64)
+        b = g.info.b_cms
+    finally:
+        g.close()
+    pix_area = (fov / npx) ** 2
+    img = maps.sum(axis=(1, 2)) * pix_area          # integrated over the image
+    vol = em.sum(axis=0)                            # volume-integrated emissivity
+    assert np.allclose(img, vol, rtol=0.01)
+    vmin, dv, nch = p.channels
+    v = vmin + (np.arange(nch) + 0.5) * dv
+    shape = np.exp(-((v + 1e5) / b) ** 2)
+    assert abs(v[np.argmax(img)] + 1e5) <= dv
+    assert np.max(np.abs(img / img.sum() - shape / shape.sum())) / np.max(shape / shape.sum()) < 0.02
