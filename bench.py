@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-raytrace", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serial", dest="pipeline", action="store_false",
                     help="issue every step on one stream (no overlap of one step's tail with the next)")
     return ap.parse_args()
@@ -180,6 +181,71 @@ def bench_raytrace(args, dev):
             "rays_per_s": rays / ms * 1e3, "channel_rays_per_s": rays * RT_CHANNELS / ms * 1e3,
             "ms_per_pass": ms, "passes": reps, "gpu_launches_per_pass": RT_CAMERAS,
             "emissivity_bytes": RT_CAMERAS * RT_GRID ** 3 * RT_CHANNELS * 4}
+
+
+BATCH_MODELS = 64
+BATCH_PACKETS = 300_000
+BATCH_TAU = (1e3, 1e5)
+
+
+def bench_batch(args, dev):
+    """Config-4 model set at the scaled size (64 uniform spheres, sides in
+    {32, 48, 64, 96, 128}, tau0 log-uniform in [1e3, 1e5], a log-uniform in
+    [1e-4, 1e-2], v_max uniform in [-300, 300] km/s, 3e5 packets split in
+    proportion to tau0): one persistent batched launch (launch parameters
+    from the autotuner), the same launch replayed from a CUDA graph, and one
+    launch per model on one stream, each over the same packets."""
+    import torch
+    import paper_2608_09340_gb300 as krl
+    from paper_2608_09340_gb300 import autotune
+    import workloads as W
+    ms = W.model_set(n_models=BATCH_MODELS, total_packets=BATCH_PACKETS, tau_range=BATCH_TAU)
+    grids = [krl.Grid(p, device=dev) for p in ms]
+    pk = [p.n_packets for p in ms]
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3
+
+    def total_scat():
+        return sum(int(g.tally("stats")[4]) for g in grids)
+
+    try:
+        b = krl.Batch(grids)
+        best, _ = autotune.tune_batch(b, pk)
+        b.run(pk, seed=7, **best)                                  # warm-up
+        for g in grids:
+            g.reset()
+        t_batch = timed(lambda: b.run(pk, seed=7, **best))
+        scat = total_scat()
+        for g in grids:
+            g.reset()
+        s = torch.cuda.Stream(device=dev)
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize(dev)
+        with torch.cuda.graph(graph, stream=s):
+            b.run(pk, seed=7, stream=s, **best)
+        t_graph = timed(lambda: graph.replay())
+        assert total_scat() == scat
+        for g in grids:
+            g.reset()
+        t_single = timed(lambda: [g.run(n=n, seed=7, want_stats=False) for g, n in zip(grids, pk)])
+        assert total_scat() == scat
+        b.close()
+    finally:
+        for g in grids:
+            g.close()
+    return {"workload": f"{BATCH_MODELS} spheres, tau0 log-U{list(BATCH_TAU)}, {BATCH_PACKETS} packets",
+            "scatterings": scat, "tuned": best,
+            "batched_scat_per_s": scat / t_batch, "graph_scat_per_s": scat / t_graph,
+            "per_model_scat_per_s": scat / t_single, "speedup_vs_per_model": t_single / t_batch,
+            "s_batched": t_batch, "s_graph": t_graph, "s_per_model": t_single}
 
 
 def run_reference(args, rank):
@@ -360,6 +426,9 @@ def main():
     rt = None
     if rank == 0 and not args.no_raytrace:
         rt = bench_raytrace(args, dev)
+    bt = None
+    if rank == 0 and not args.no_batch:
+        bt = bench_batch(args, dev)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -373,7 +442,7 @@ def main():
                        "l2": "flushed before every timed step (256 MiB write)",
                        "steps_issue": "two streams, alternating" if args.pipeline else "one stream",
                        "parallelism": f"packet-id shards x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "raytrace": rt,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "raytrace": rt, "batch": bt,
             "gpu_launches": 2 * args.steps, "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

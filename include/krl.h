@@ -245,6 +245,38 @@ KRL_API size_t krl_tally_bytes(const krl_grid* g, krl_tally_kind kind);
 /* Zero all tallies and counters. Enqueued on `s`. */
 KRL_API krl_status krl_tallies_reset(krl_grid* g, krl_stream s);
 
+/* ------------------------------------------------------------------ batched models */
+
+typedef struct krl_batch krl_batch;
+
+/*
+ * A set of grids (independent models, each with its own line and tables)
+ * to be run together by krl_batch_run. Uploads nothing yet; synchronises
+ * `s`. The grids must live on the current device and stay alive, and their
+ * lines must not change (krl_batch_run checks) while the batch is used.
+ */
+KRL_API krl_status krl_batch_create(krl_batch** out, krl_grid* const* grids, int n_models, krl_stream s);
+KRL_API krl_status krl_batch_destroy(krl_batch* b);
+
+/*
+ * Run packets[m] packets with ids [first_ids[m], first_ids[m] + packets[m])
+ * (first_ids may be NULL: all 0) of every model m under one key `seed`, in
+ * ONE persistent launch: each CTA takes the lowest-numbered model that still
+ * has packet ids, stages that model's tables, runs its warps on it until its
+ * ids run out, and moves on, so the models' tails overlap. Each packet's
+ * random stream, and therefore every tally, is exactly what krl_run_packets
+ * on that grid with the same (seed, ids) gives. Tallies accumulate into each
+ * grid. stats (host [n_models] or NULL): per-model counters; when given the
+ * call synchronises `s`. The call first waits for `s` (it rewrites a pinned
+ * argument mirror the previous run's copy reads), then enqueues a copy of
+ * the arguments, the launch and the counter updates; captured into a CUDA
+ * graph (stats must then be NULL, and the stream must be idle when the
+ * capture begins), each replay copies the arguments of the captured call
+ * again and reruns the same packets.
+ */
+KRL_API krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* first_ids, uint64_t seed,
+                                 const krl_tune* tune, krl_run_stats* stats, krl_stream s);
+
 /* ------------------------------------------------------------------ channel maps */
 
 typedef struct {

@@ -88,7 +88,8 @@ assert RECORD_DTYPE.itemsize == 20
 
 EXPORTS = ["krl_last_error", "krl_version", "krl_grid_create", "krl_grid_destroy", "krl_line_set",
            "krl_line_info_get", "krl_run_packets", "krl_tallies_get", "krl_tally_bytes", "krl_tallies_reset",
-           "krl_emission_cdf_noalloc", "krl_raytrace_channels"]
+           "krl_emission_cdf_noalloc", "krl_raytrace_channels", "krl_batch_create", "krl_batch_run",
+           "krl_batch_destroy"]
 
 _lib_handle = None
 
@@ -118,9 +119,13 @@ def load_library(path: str | None = None):
     lib.krl_tallies_reset.argtypes = [vp, vp]
     lib.krl_emission_cdf_noalloc.argtypes = [vp, C.c_int, vp, vp]
     lib.krl_raytrace_channels.argtypes = [vp, C.POINTER(krl_raytrace_desc), vp, vp]
+    lib.krl_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
+    lib.krl_batch_destroy.argtypes = [vp]
+    lib.krl_batch_run.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_uint64,
+                                  C.POINTER(krl_tune), C.POINTER(krl_run_stats), vp]
     for name in ("krl_grid_create", "krl_grid_destroy", "krl_line_set", "krl_line_info_get",
                  "krl_run_packets", "krl_tallies_get", "krl_tallies_reset", "krl_emission_cdf_noalloc",
-                 "krl_raytrace_channels"):
+                 "krl_raytrace_channels", "krl_batch_create", "krl_batch_destroy", "krl_batch_run"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib_handle = lib
@@ -320,6 +325,42 @@ class Grid:
                               jline.data_ptr() if jline is not None else None)
         krl_raytrace_channels(self.handle, d, maps, stream)
         return maps
+
+
+class Batch:
+    """krl_batch over several Grids: all models in one persistent launch."""
+
+    def __init__(self, grids, stream=None):
+        lib = load_library()
+        self.grids = list(grids)
+        arr = (C.c_void_p * len(self.grids))(*[g.handle.value for g in self.grids])
+        h = C.c_void_p()
+        _check(lib.krl_batch_create(C.byref(h), arr, len(self.grids), _stream_handle(stream)))
+        self.handle = h
+
+    def run(self, packets, first_ids=None, seed: int = 0, precision: int = KRL_PREC_FP32, block: int = 0,
+            ctas_per_sm: int = 0, refill_min: int = 0, max_iters: int = 0, want_stats: bool = False, stream=None):
+        n = len(self.grids)
+        pk = (C.c_uint64 * n)(*[int(v) for v in packets])
+        fi = (C.c_uint64 * n)(*[int(v) for v in first_ids]) if first_ids is not None else None
+        tune = krl_tune(precision, block, ctas_per_sm, refill_min, max_iters)
+        st = (krl_run_stats * n)() if want_stats else None
+        rc = load_library().krl_batch_run(self.handle, pk, fi, int(seed) & ((1 << 64) - 1), C.byref(tune),
+                                          st, _stream_handle(stream))
+        if not (rc == KRL_ERR_BUDGET and st is not None):
+            _check(rc)
+        return (list(st) if st is not None else None), rc
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            _check(load_library().krl_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def records_to_numpy(rec_tensor) -> np.ndarray:

@@ -1,0 +1,72 @@
+"""Launch-parameter autotuner for the packet walk.
+
+Times short pilot runs (a fraction of each model's packets, under ids that
+the real run does not use) for every candidate (block size, refill
+threshold, CTAs per SM) and returns the fastest. Pilot tallies are
+discarded (the tallies are reset afterwards), so tuning does not change
+what a later run accumulates.
+"""
+from __future__ import annotations
+
+import itertools
+
+DEFAULT_SPACE = {
+    "block": (256, 512),
+    "refill_min": (1, 4, 16),
+    "ctas_per_sm": (0, 1),          # 0: as many as fit
+}
+
+PILOT_FIRST_ID = 1 << 48            # pilot packets use ids far from any real run
+
+
+def _candidates(space):
+    keys = list(space)
+    for vals in itertools.product(*(space[k] for k in keys)):
+        yield dict(zip(keys, vals))
+
+
+def _time(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def tune_batch(batch, packets, fraction: float = 0.2, space=None, seed: int = 12345):
+    """Best {block, refill_min, ctas_per_sm} for `batch` (a Batch) and the
+    per-model packet counts `packets`; returns (best, timings)."""
+    space = space or DEFAULT_SPACE
+    pilot = [max(1, int(n * fraction)) for n in packets]
+    first = [PILOT_FIRST_ID] * len(pilot)
+    timings = []
+    for cand in _candidates(space):
+        try:                            # a block the walk does not support raises: skip it
+            ms = _time(lambda: batch.run(pilot, first_ids=first, seed=seed, **cand))
+        except Exception:
+            continue
+        timings.append((ms, cand))
+    for g in batch.grids:
+        g.reset()
+    timings.sort(key=lambda t: t[0])
+    return timings[0][1], timings
+
+
+def tune_grid(grid, n: int, fraction: float = 0.05, space=None, seed: int = 12345):
+    """Best launch parameters for krl_run_packets on one grid."""
+    space = space or DEFAULT_SPACE
+    pilot = max(1, int(n * fraction))
+    timings = []
+    for cand in _candidates(space):
+        try:
+            ms = _time(lambda: grid.run(n=pilot, first=PILOT_FIRST_ID, seed=seed, want_stats=False, **cand))
+        except Exception:
+            continue
+        timings.append((ms, cand))
+    grid.reset()
+    timings.sort(key=lambda t: t[0])
+    return timings[0][1], timings

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "krl_internal.cuh"
 
@@ -27,6 +28,7 @@ struct krl_grid {
     bool has_vel = false;
     // line
     bool line_ok = false;
+    unsigned line_gen = 0;     // bumped by every krl_line_set (batches check it)
     krl_line_desc line{};
     krl_line_info info{};
     bool has_rtab = false;
@@ -178,6 +180,95 @@ krl_status zero_tallies(krl_grid* g, cudaStream_t s)
         size_t n = tally_elems(g, (krl_tally_kind)k, &esz);
         if (n) KRL_CUDA(cudaMemsetAsync((void*)tally_ptr(g, (krl_tally_kind)k), 0, n * esz, s), "zero tallies");
     }
+    return KRL_OK;
+}
+
+
+unsigned features_of(const krl_grid* g)
+{
+    const krl_line_desc& L = g->line;
+    unsigned f = 0;
+    if (g->has_vel) f |= F_VEL;
+    if (L.tally_flags & KRL_TALLY_SCATMAP) f |= F_SCAT;
+    if ((L.tally_flags & (KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS)) || g->eps) f |= F_RICH;
+    return f;
+}
+
+// The walk's argument block for one grid (work counter and run counters are
+// filled in by the caller).
+void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_id, uint64_t seed, const krl_tune& T,
+               krl_packet_record* records)
+{
+    const krl_line_desc& L = g->line;
+    unsigned rich = L.tally_flags & (KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS);
+    if (g->eps) rich |= kRichEps;
+    A.cells = g->cells;
+    A.eps = g->eps;
+    A.nx = g->nx;
+    A.ny = g->ny;
+    A.nz = g->nz;
+    A.ncell = g->ncell;
+    A.periodic = g->periodic;
+    A.a = (float)g->info.a;
+    A.H0 = g->tab.H0;
+    A.voigt_lnH = g->tab.voigt_lnH;
+    A.us_x = g->tab.us_x;
+    A.us_lncdf = g->tab.us_lncdf;
+    A.us_guide = g->tab.us_guide;
+    A.rtab = g->tab.rtab;
+    A.src_kind = L.src_kind;
+    A.src_profile = L.src_profile;
+    A.src_axis = L.src_axis;
+    A.band_axis = L.band_axis;
+    for (int k = 0; k < 3; ++k) A.src_pos[k] = L.src_pos[k];
+    A.src_plane = L.src_plane;
+    A.band_lo = L.band_lo;
+    A.band_hi = L.band_hi;
+    A.src_cdf = g->src_cdf;
+    A.spec_lo = L.spec_xmin;
+    A.spec_hi = L.spec_xmax;
+    A.spec_n = L.spec_nbins;
+    A.n_ch = L.n_ch;
+    A.ch_x0 = (float)(L.ch_vmin_cms / g->info.b_cms);
+    A.ch_dx = (float)(L.ch_dv_cms / g->info.b_cms);
+    A.n_cam = L.n_cam;
+    for (int m = 0; m < L.n_cam; ++m) {
+        double th = L.cam_theta[m], ph = L.cam_phi[m];
+        A.cam[m][0] = (float)(sin(th) * cos(ph));
+        A.cam[m][1] = (float)(sin(th) * sin(ph));
+        A.cam[m][2] = (float)cos(th);
+    }
+    A.rich = rich;
+    A.spec_w = g->spec_w;
+    A.spec_c = g->spec_c;
+    A.scat = g->scat;
+    A.exc = g->exc;
+    A.J = g->J;
+    A.emiss = g->emiss;
+    A.rec = records;
+    A.first = first_id;
+    A.n = n;
+    A.k0 = (unsigned)(seed & 0xffffffffu);
+    A.k1 = (unsigned)(seed >> 32);
+    A.max_iters = T.max_iters;
+    A.refill_min = T.refill_min;
+}
+
+krl_status resolve_tune(const krl_tune* tune, krl_tune& T)
+{
+    T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 1ull << 40};
+    if (tune) {
+        if (tune->precision != KRL_PREC_FP32 && tune->precision != KRL_PREC_FP64)
+            return fail(KRL_ERR_ARG, "unknown precision");
+        T.precision = tune->precision;
+        if (tune->block) T.block = tune->block;
+        if (tune->ctas_per_sm) T.ctas_per_sm = tune->ctas_per_sm;
+        if (tune->refill_min) T.refill_min = tune->refill_min;
+        if (tune->max_iters) T.max_iters = tune->max_iters;
+    }
+    if (T.block && (T.block < 32 || T.block > 512 || T.block % 32))
+        return fail(KRL_ERR_ARG, "block must be a multiple of 32 in [32, 512]");
+    if (T.refill_min < 1 || T.refill_min > 32) return fail(KRL_ERR_ARG, "refill_min must be in [1, 32]");
     return KRL_OK;
 }
 
@@ -390,6 +481,7 @@ krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
     }
     g->info.H0 = h0;
     g->line_ok = true;
+    ++g->line_gen;
     return KRL_OK;
 }
 
@@ -407,29 +499,13 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     cudaStream_t s = (cudaStream_t)st;
     if (!g) return fail(KRL_ERR_ARG, "krl_run_packets: NULL grid");
     if (!g->line_ok) return fail(KRL_ERR_STATE, "krl_run_packets before krl_line_set");
-    krl_tune T{KRL_PREC_FP32, 512, 0, 1, 1ull << 40};
-    if (tune) {
-        if (tune->precision != KRL_PREC_FP32 && tune->precision != KRL_PREC_FP64)
-            return fail(KRL_ERR_ARG, "unknown precision");
-        T.precision = tune->precision;
-        if (tune->block) T.block = tune->block;
-        if (tune->ctas_per_sm) T.ctas_per_sm = tune->ctas_per_sm;
-        if (tune->refill_min) T.refill_min = tune->refill_min;
-        if (tune->max_iters) T.max_iters = tune->max_iters;
-    }
-    if (T.block < 32 || T.block > 512 || T.block % 32) return fail(KRL_ERR_ARG, "block must be a multiple of 32 in [32, 512]");
-    if (T.refill_min < 1 || T.refill_min > 32) return fail(KRL_ERR_ARG, "refill_min must be in [1, 32]");
+    krl_tune T;
+    krl_status ts = resolve_tune(tune, T);
+    if (ts != KRL_OK) return ts;
     if (stats) memset(stats, 0, sizeof(*stats));
     if (n == 0) return KRL_OK;
 
-    const krl_line_desc& L = g->line;
-    unsigned f = 0;
-    if (g->has_vel) f |= F_VEL;
-    if (L.tally_flags & KRL_TALLY_SCATMAP) f |= F_SCAT;
-    unsigned rich = L.tally_flags & (KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS);
-    if (g->eps) rich |= kRichEps;
-    if (rich) f |= F_RICH;
-
+    const unsigned f = features_of(g);
     const int maxb = transport_max_block(T.precision, f);
     if (!tune || !tune->block) T.block = maxb;
     else if (T.block > maxb) return fail(KRL_ERR_ARG, "block %d exceeds %d for this walk", T.block, maxb);
@@ -439,61 +515,12 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     int grid = g->num_sms * per_sm;
 
     TransportArgs A{};
-    A.cells = g->cells;
-    A.eps = g->eps;
-    A.nx = g->nx;
-    A.ny = g->ny;
-    A.nz = g->nz;
-    A.ncell = g->ncell;
-    A.periodic = g->periodic;
-    A.a = (float)g->info.a;
-    A.H0 = g->tab.H0;
-    A.voigt_lnH = g->tab.voigt_lnH;
-    A.us_x = g->tab.us_x;
-    A.us_lncdf = g->tab.us_lncdf;
-    A.us_guide = g->tab.us_guide;
-    A.rtab = g->tab.rtab;
-    A.src_kind = L.src_kind;
-    A.src_profile = L.src_profile;
-    A.src_axis = L.src_axis;
-    A.band_axis = L.band_axis;
-    for (int k = 0; k < 3; ++k) A.src_pos[k] = L.src_pos[k];
-    A.src_plane = L.src_plane;
-    A.band_lo = L.band_lo;
-    A.band_hi = L.band_hi;
-    A.src_cdf = g->src_cdf;
-    A.spec_lo = L.spec_xmin;
-    A.spec_hi = L.spec_xmax;
-    A.spec_n = L.spec_nbins;
-    A.n_ch = L.n_ch;
-    A.ch_x0 = (float)(L.ch_vmin_cms / g->info.b_cms);
-    A.ch_dx = (float)(L.ch_dv_cms / g->info.b_cms);
-    A.n_cam = L.n_cam;
-    for (int m = 0; m < L.n_cam; ++m) {
-        double th = L.cam_theta[m], ph = L.cam_phi[m];
-        A.cam[m][0] = (float)(sin(th) * cos(ph));
-        A.cam[m][1] = (float)(sin(th) * sin(ph));
-        A.cam[m][2] = (float)cos(th);
-    }
-    A.rich = rich;
-    A.spec_w = g->spec_w;
-    A.spec_c = g->spec_c;
-    A.scat = g->scat;
-    A.exc = g->exc;
-    A.J = g->J;
-    A.emiss = g->emiss;
+    fill_args(g, A, n, first_id, seed, T, records);
     const int slot = (int)(g->run_seq++ % kSlots);
     unsigned long long* slot_stats = g->run_stats + (size_t)slot * ST_N;
     unsigned long long* slot_next = g->next + slot;
     A.stats = slot_stats;
     A.next = slot_next;
-    A.rec = records;
-    A.first = first_id;
-    A.n = n;
-    A.k0 = (unsigned)(seed & 0xffffffffu);
-    A.k1 = (unsigned)(seed >> 32);
-    A.max_iters = T.max_iters;
-    A.refill_min = T.refill_min;
 
     KRL_CUDA(cudaMemsetAsync(slot_next, 0, sizeof(unsigned long long), s), "reset work counter");
     KRL_CUDA(cudaMemsetAsync(slot_stats, 0, ST_N * sizeof(unsigned long long), s), "reset run counters");
@@ -570,6 +597,135 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
     A.npix_y = d->npix_y;
     A.maps = maps;
     KRL_CUDA(launch_raytrace(A, (cudaStream_t)st), "ray trace launch");
+    return KRL_OK;
+}
+
+}  // extern "C"
+
+struct krl_batch {
+    int n = 0;
+    int device = 0;
+    int num_sms = 0;
+    std::vector<krl_grid*> grids;
+    std::vector<unsigned> gens;
+    TransportArgs* h_args = nullptr;          // pinned mirror, updated by each run
+    TransportArgs* d_args = nullptr;
+    unsigned long long* d_counts = nullptr;   // [n] work counters, then [n][ST_N] run counters
+    unsigned long long** d_dst = nullptr;     // [n] each grid's cumulative counters
+    int* d_cursor = nullptr;
+    unsigned features = 0;
+};
+
+extern "C" {
+
+krl_status krl_batch_destroy(krl_batch* b)
+{
+    if (!b) return KRL_OK;
+    cudaDeviceSynchronize();
+    if (b->h_args) cudaFreeHost(b->h_args);
+    dfree(b->d_args);
+    dfree(b->d_counts);
+    dfree(b->d_dst);
+    dfree(b->d_cursor);
+    delete b;
+    return KRL_OK;
+}
+
+krl_status krl_batch_create(krl_batch** out, krl_grid* const* grids, int n_models, krl_stream st)
+{
+    if (!out || !grids || n_models < 1) return fail(KRL_ERR_ARG, "krl_batch_create: bad arguments");
+    *out = nullptr;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int m = 0; m < n_models; ++m) {
+        if (!grids[m]) return fail(KRL_ERR_ARG, "grid %d is NULL", m);
+        if (!grids[m]->line_ok) return fail(KRL_ERR_STATE, "grid %d has no line", m);
+        if (grids[m]->device != dev) return fail(KRL_ERR_ARG, "grid %d lives on another device", m);
+    }
+    krl_batch* b = new (std::nothrow) krl_batch();
+    if (!b) return fail(KRL_ERR_OOM, "host allocation failed");
+    b->n = n_models;
+    b->device = dev;
+    b->num_sms = grids[0]->num_sms;
+    b->grids.assign(grids, grids + n_models);
+    for (int m = 0; m < n_models; ++m) {
+        b->gens.push_back(grids[m]->line_gen);
+        b->features |= features_of(grids[m]);
+    }
+    const size_t n = (size_t)n_models;
+    cudaError_t e = cudaMallocHost((void**)&b->h_args, n * sizeof(TransportArgs));
+    if (e == cudaSuccess) e = dalloc(&b->d_args, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_counts, n * (1 + ST_N));
+    if (e == cudaSuccess) e = dalloc(&b->d_dst, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_cursor, 1);
+    if (e == cudaSuccess) {
+        std::vector<unsigned long long*> dst(n);
+        for (size_t m = 0; m < n; ++m) dst[m] = grids[m]->stats;
+        e = cudaMemcpyAsync(b->d_dst, dst.data(), n * sizeof(void*), cudaMemcpyHostToDevice, (cudaStream_t)st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)st);
+    }
+    if (e != cudaSuccess) {
+        krl_batch_destroy(b);
+        return cuda_fail(e, "krl_batch_create");
+    }
+    *out = b;
+    return KRL_OK;
+}
+
+krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* first_ids, uint64_t seed,
+                         const krl_tune* tune, krl_run_stats* stats, krl_stream st)
+{
+    cudaStream_t s = (cudaStream_t)st;
+    if (!b || !packets) return fail(KRL_ERR_ARG, "krl_batch_run: NULL argument");
+    for (int m = 0; m < b->n; ++m)
+        if (!b->grids[m]->line_ok || b->grids[m]->line_gen != b->gens[m])
+            return fail(KRL_ERR_STATE, "grid %d's line changed since krl_batch_create", m);
+    krl_tune T;
+    krl_status ts = resolve_tune(tune, T);
+    if (ts != KRL_OK) return ts;
+    const unsigned f = b->features;
+    const int maxb = transport_max_block(T.precision, f);
+    if (!T.block) T.block = maxb;
+    else if (T.block > maxb) return fail(KRL_ERR_ARG, "block %d exceeds %d for this walk", T.block, maxb);
+    const int occ = transport_occupancy(T.precision, f, T.block);
+    if (occ < 1) return fail(KRL_ERR_CUDA, "transport kernel cannot be resident at block %d", T.block);
+    const int per_sm = T.ctas_per_sm > 0 ? (T.ctas_per_sm < occ ? T.ctas_per_sm : occ) : occ;
+    const int grid = b->num_sms * per_sm;
+    const size_t n = (size_t)b->n;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    KRL_CUDA(cudaStreamIsCapturing(s, &cap), "krl_batch_run");
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    if (capturing && stats) return fail(KRL_ERR_ARG, "stats cannot be read while the stream is being captured");
+    // the pinned mirror is rewritten here; wait until the previous run's copy
+    // has read it (a capture records the copy instead of running it)
+    if (!capturing) KRL_CUDA(cudaStreamSynchronize(s), "krl_batch_run");
+    for (size_t m = 0; m < n; ++m) {
+        TransportArgs& A = b->h_args[m];
+        A = TransportArgs{};
+        fill_args(b->grids[m], A, packets[m], first_ids ? first_ids[m] : 0, seed, T, nullptr);
+        A.next = b->d_counts + m;
+        A.stats = b->d_counts + n + m * ST_N;
+    }
+    KRL_CUDA(cudaMemcpyAsync(b->d_args, b->h_args, n * sizeof(TransportArgs), cudaMemcpyHostToDevice, s),
+             "upload model arguments");
+    KRL_CUDA(cudaMemsetAsync(b->d_counts, 0, n * (1 + ST_N) * sizeof(unsigned long long), s), "reset counters");
+    KRL_CUDA(cudaMemsetAsync(b->d_cursor, 0, sizeof(int), s), "reset cursor");
+    BatchArgs B{b->d_args, b->n, b->d_cursor};
+    KRL_CUDA(launch_transport_batch(B, T.precision, f, grid, T.block, s), "batch launch");
+    KRL_CUDA(add_counters_batch(b->d_dst, b->d_counts + n, b->n, s), "accumulate counters");
+    if (stats) {
+        std::vector<unsigned long long> h(n * ST_N);
+        KRL_CUDA(cudaMemcpyAsync(h.data(), b->d_counts + n, h.size() * 8, cudaMemcpyDeviceToHost, s), "read counters");
+        KRL_CUDA(cudaStreamSynchronize(s), "krl_batch_run");
+        unsigned long long stuck = 0;
+        for (size_t m = 0; m < n; ++m) {
+            const unsigned long long* c = h.data() + m * ST_N;
+            stats[m] = krl_run_stats{c[ST_EMITTED], c[ST_ESCAPED], c[ST_DESTROYED], c[ST_STUCK], c[ST_SCAT],
+                                     c[ST_CROSS]};
+            stuck += c[ST_STUCK];
+        }
+        if (stuck) return fail(KRL_ERR_BUDGET, "%llu packets exhausted max_iters", stuck);
+    }
     return KRL_OK;
 }
 

@@ -96,6 +96,16 @@ constexpr unsigned kRichEps = 1u << 16;
 // Launch the walk (transport.cu). grid/block chosen by the caller.
 cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned features,
                              int grid, int block, cudaStream_t s);
+// Many models in one launch: models[m] holds model m's full argument block
+// (its own work counter `next`, run counters `stats`, tables and tallies).
+struct BatchArgs {
+    const TransportArgs* models;   // device [n_models]
+    int n_models;
+    int* cursor;                   // device: lowest model that may still have work
+};
+cudaError_t launch_transport_batch(const BatchArgs& B, int precision, unsigned features, int grid, int block,
+                                   cudaStream_t s);
+
 // Occupancy of one instantiation (CTAs per SM at this block size).
 int transport_occupancy(int precision, unsigned features, int block);
 // Largest CTA the instantiation is compiled for (512 lean FP32, else 256).
@@ -156,6 +166,10 @@ cudaError_t validate_field(const float* f, int n, bool allow_negative, int* bad,
 cudaError_t emission_cdf(const float* rate, int n, double* cdf, double* work, size_t work_doubles,
                          int* bad, cudaStream_t s);
 size_t emission_cdf_work_doubles(int n);
+
+// dst[m][k] += src[m * ST_N + k] for m < n_models, k < ST_N (64-bit counters).
+cudaError_t add_counters_batch(unsigned long long* const* dst, const unsigned long long* src, int n_models,
+                               cudaStream_t s);
 
 // out[i] += in[i], 64-bit counters.
 cudaError_t add_counters(unsigned long long* out, const unsigned long long* in, int n, cudaStream_t s);

@@ -261,7 +261,23 @@ __global__ void k_add_counters(unsigned long long* out, const unsigned long long
     if (i < n && in[i]) atomicAdd(out + i, in[i]);   // runs on other streams may add too
 }
 
+__global__ void k_add_counters_batch(unsigned long long* const* dst, const unsigned long long* src, int n_models)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_models * ST_N) return;
+    const unsigned long long v = src[i];
+    if (v) atomicAdd(dst[i / ST_N] + (i % ST_N), v);
+}
+
 }  // namespace
+
+cudaError_t add_counters_batch(unsigned long long* const* dst, const unsigned long long* src, int n_models,
+                               cudaStream_t s)
+{
+    const int n = n_models * ST_N;
+    k_add_counters_batch<<<(n + 127) / 128, 128, 0, s>>>(dst, src, n_models);
+    return cudaGetLastError();
+}
 
 size_t line_tables_work_doubles() { return 64 + (size_t)kRnX * (kUsNu - 1); }
 

@@ -459,7 +459,7 @@ __device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xc
 template <typename R, unsigned F>
 __device__ __forceinline__ void flush_visit(const TransportArgs& A, Pkt<R>& p)
 {
-    if ((F & F_SCAT) && p.vis_scat) atomicAdd(A.scat + p.c, (unsigned long long)p.vis_scat);
+    if ((F & F_SCAT) && p.vis_scat && A.scat) atomicAdd(A.scat + p.c, (unsigned long long)p.vis_scat);
     if ((F & F_RICH) && (A.rich & KRL_TALLY_EXC) && p.vis_exc != (R)0) atomicAdd(A.exc + p.c, (double)p.vis_exc);
     p.vis_scat = 0;
     p.vis_exc = (R)0;
@@ -479,11 +479,13 @@ __device__ __forceinline__ T warp_sum(T v)
 template <typename R, unsigned F>
 constexpr int max_block() { return (sizeof(R) == 4 && !(F & F_RICH)) ? 512 : 256; }
 
+// One model's walk by the whole CTA: stage the model's tables in shared
+// memory, run packets until the model's id counter is exhausted and every
+// lane has finished, then add the counters. Every thread of the CTA calls it.
 template <typename R, unsigned F>
-__global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport(const TransportArgs A)
+__device__ __forceinline__ void run_model(const TransportArgs& A, float* sm)
 {
     using O = Ops<R>;
-    extern __shared__ float sm[];
     for (int i = threadIdx.x; i < kVoigtN; i += blockDim.x) sm[kSmemVoigt + i] = A.voigt_lnH[i];
     for (int i = threadIdx.x; i < kUsNx; i += blockDim.x) sm[kSmemUsX + i] = A.us_x[i];
     for (int i = threadIdx.x; i < kUsNx * kUsNu; i += blockDim.x) sm[kSmemUsC + i] = A.us_lncdf[i];
@@ -665,6 +667,56 @@ __global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport(const Transp
 }
 
 template <typename R, unsigned F>
+__global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport(const __grid_constant__ TransportArgs A)
+{
+    extern __shared__ float sm[];
+    run_model<R, F>(A, sm);
+}
+
+// The lowest-numbered model that still has unassigned packet ids, or -1.
+// The shared cursor only moves forward, so the loop ends within n_models
+// steps.
+__device__ int next_model(const BatchArgs& B)
+{
+    int m = atomicAdd(B.cursor, 0);
+    while (m < B.n_models) {
+        const unsigned long long used = atomicAdd(B.models[m].next, 0ull);
+        if (used < B.models[m].n) return m;
+        atomicCAS(B.cursor, m, m + 1);
+        const int m2 = atomicAdd(B.cursor, 0);
+        m = m2 > m ? m2 : m + 1;
+    }
+    return -1;
+}
+
+// Many independent models (grids) in one persistent launch: each CTA takes
+// the lowest model that still has packets, stages that model's tables,
+// runs its warps on it until its ids run out, drains, and takes the next.
+// CTAs finish models at different times, so one model's tail overlaps the
+// next model's bulk instead of idling the device as separate launches do.
+template <typename R, unsigned F>
+__global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport_batch(const __grid_constant__ BatchArgs B)
+{
+    extern __shared__ float sm[];
+    __shared__ TransportArgs sA;
+    __shared__ int s_model;
+    for (;;) {
+        if (threadIdx.x == 0) s_model = next_model(B);
+        __syncthreads();
+        const int m = s_model;
+        if (m < 0) break;
+        {
+            const int* src = reinterpret_cast<const int*>(B.models + m);
+            int* dst = reinterpret_cast<int*>(&sA);
+            for (int i = threadIdx.x; i < (int)(sizeof(TransportArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        run_model<R, F>(sA, sm);
+        __syncthreads();     // every warp done before the tables are replaced
+    }
+}
+
+template <typename R, unsigned F>
 cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t s)
 {
     if (block > max_block<R, F>()) return cudaErrorInvalidConfiguration;
@@ -676,6 +728,21 @@ cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t
         configured = true;
     }
     kern<<<grid, block, kSmemBytes, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename R, unsigned F>
+cudaError_t launch_batch_one(const BatchArgs& B, int grid, int block, cudaStream_t s)
+{
+    if (block > max_block<R, F>()) return cudaErrorInvalidConfiguration;
+    auto kern = k_transport_batch<R, F>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<grid, block, kSmemBytes, s>>>(B);
     return cudaGetLastError();
 }
 
@@ -706,6 +773,21 @@ cudaError_t dispatch(const TransportArgs& A, unsigned f, int grid, int block, cu
 }
 
 template <typename R>
+cudaError_t dispatch_batch(const BatchArgs& B, unsigned f, int grid, int block, cudaStream_t s)
+{
+    switch (f & 7u) {
+    case 0: return launch_batch_one<R, 0>(B, grid, block, s);
+    case 1: return launch_batch_one<R, 1>(B, grid, block, s);
+    case 2: return launch_batch_one<R, 2>(B, grid, block, s);
+    case 3: return launch_batch_one<R, 3>(B, grid, block, s);
+    case 4: return launch_batch_one<R, 4>(B, grid, block, s);
+    case 5: return launch_batch_one<R, 5>(B, grid, block, s);
+    case 6: return launch_batch_one<R, 6>(B, grid, block, s);
+    default: return launch_batch_one<R, 7>(B, grid, block, s);
+    }
+}
+
+template <typename R>
 int occ_dispatch(unsigned f, int block)
 {
     switch (f & 7u) {
@@ -727,6 +809,13 @@ cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned fea
 {
     return precision == KRL_PREC_FP64 ? dispatch<double>(A, features, grid, block, s)
                                       : dispatch<float>(A, features, grid, block, s);
+}
+
+cudaError_t launch_transport_batch(const BatchArgs& B, int precision, unsigned features, int grid, int block,
+                                   cudaStream_t s)
+{
+    return precision == KRL_PREC_FP64 ? dispatch_batch<double>(B, features, grid, block, s)
+                                      : dispatch_batch<float>(B, features, grid, block, s);
 }
 
 int transport_max_block(int precision, unsigned features)

@@ -1,0 +1,114 @@
+"""Many models in one persistent launch (krl_batch_run) give exactly the
+tallies of one krl_run_packets launch per model, also when the batched
+launch is captured into a CUDA graph and replayed."""
+import numpy as np
+import pytest
+
+import workloads as W
+from _gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _models():
+    ms = [W.sphere(vmax_kms=120.0, tau0=3e4, n=24, n_packets=3000, tallies=("scatmap",)),
+          W.sphere(vmax_kms=0.0, tau0=2e3, n=16, n_packets=700, tallies=("scatmap",)),
+          W.slab(tau0=5e3, a=1e-2, n_packets=1500),
+          W.sphere(vmax_kms=-250.0, tau0=1e5, n=32, n_packets=2500, a=1e-3, tallies=("scatmap",)),
+          W.box(tau0=50.0, n=8, n_packets=4000, tallies=("scatmap", "exc"))]
+    for i, p in enumerate(ms):
+        p.seed = 11
+    return ms
+
+
+def _tallies(g):
+    out = {k: g.tally(k) for k in ("spec_n", "scatmap", "stats", "exc")}
+    return {k: (None if v is None else v.cpu().numpy()) for k, v in out.items()}
+
+
+def test_batch_equals_one_launch_per_model():
+    krl = need_gpu()
+    import torch
+    ms = _models()
+    single = []
+    for p in ms:
+        g = krl.Grid(p)
+        g.run(first=100, seed=11, want_stats=False)
+        torch.cuda.synchronize()
+        single.append(_tallies(g))
+        g.close()
+    grids = [krl.Grid(p) for p in ms]
+    try:
+        b = krl.Batch(grids)
+        st, rc = b.run([p.n_packets for p in ms], first_ids=[100] * len(ms), seed=11, want_stats=True)
+        torch.cuda.synchronize()
+        for m, (g, ref) in enumerate(zip(grids, single)):
+            got = _tallies(g)
+            assert np.array_equal(got["spec_n"], ref["spec_n"]), m
+            assert np.array_equal(got["stats"], ref["stats"]), m
+            if ref["scatmap"] is not None:
+                assert np.array_equal(got["scatmap"], ref["scatmap"]), m
+            if ref["exc"] is not None:
+                assert np.allclose(got["exc"], ref["exc"], rtol=1e-5), m
+            assert st[m].emitted == ms[m].n_packets and st[m].scatterings == ref["stats"][4]
+        b.close()
+    finally:
+        for g in grids:
+            g.close()
+
+
+def test_batch_in_a_cuda_graph():
+    krl = need_gpu()
+    import torch
+    ms = _models()[:3]
+    grids = [krl.Grid(p) for p in ms]
+    try:
+        b = krl.Batch(grids)
+        pk = [p.n_packets for p in ms]
+        b.run(pk, seed=3)
+        torch.cuda.synchronize()
+        once = [_tallies(g) for g in grids]
+        for g in grids:
+            g.reset()
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            b.run(pk, seed=3, stream=s)
+        for g in grids:            # capture ran nothing
+            assert int(g.tally("stats").cpu()[0]) == 0
+        graph.replay()
+        graph.replay()
+        torch.cuda.synchronize()
+        for g, ref in zip(grids, once):
+            got = _tallies(g)
+            assert np.array_equal(got["spec_n"], 2 * ref["spec_n"])
+            assert np.array_equal(got["stats"], 2 * ref["stats"])
+        b.close()
+    finally:
+        for g in grids:
+            g.close()
+
+
+def test_batch_detects_a_changed_line():
+    krl = need_gpu()
+    ms = _models()[:2]
+    grids = [krl.Grid(p) for p in ms]
+    try:
+        b = krl.Batch(grids)
+        import ctypes as C
+        from paper_2608_09340_gb300 import krl_line_desc, krl_line_set
+        b.run([10, 10], seed=1)
+        # give grid 0 a new line through the C ABI
+        L = krl_line_desc()
+        L.nu0_hz, L.mass_amu, L.A_ul, L.g_u, L.g_l, L.a_fixed = 2.466e15, 1.00794, 6.265e8, 6.0, 2.0, 2e-3
+        L.src_kind, L.spec_xmin, L.spec_xmax, L.spec_nbins = 0, -30.0, 30.0, 50
+        L.src_pos = (C.c_double * 3)(12.0, 12.0, 12.0)
+        krl_line_set(grids[0].handle, L)
+        with pytest.raises(krl.KrlError) as e:
+            b.run([10, 10], seed=1)
+        assert e.value.status == krl.KRL_ERR_STATE
+        b.close()
+    finally:
+        for g in grids:
+            g.close()
