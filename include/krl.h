@@ -245,6 +245,53 @@ KRL_API size_t krl_tally_bytes(const krl_grid* g, krl_tally_kind kind);
 /* Zero all tallies and counters. Enqueued on `s`. */
 KRL_API krl_status krl_tallies_reset(krl_grid* g, krl_stream s);
 
+/* ------------------------------------------------------------------ level populations */
+
+#define KRL_MAX_LEVELS 8
+
+typedef struct {
+    int n_lev;                                       /* 2 .. KRL_MAX_LEVELS             */
+    double E_K[KRL_MAX_LEVELS];                      /* level energies / k_B [K]        */
+    double g[KRL_MAX_LEVELS];                        /* degeneracies                    */
+    double A[KRL_MAX_LEVELS][KRL_MAX_LEVELS];        /* A[u][l] (u > l) [s^-1]; > 0
+                                                        marks a radiative line          */
+    double k_coll[KRL_MAX_LEVELS][KRL_MAX_LEVELS];   /* k[u][l] (u > l) collisional
+                                                        de-excitation [cm^3 s^-1]       */
+    double mass_amu;
+    const float* n_mol;                              /* device [ncell] molecule density */
+} krl_levels_desc;
+
+/*
+ * Statistical equilibrium per cell (Sec. 2.1.3; Eq. boltzmann generalised
+ * to n levels), FP64, one thread per cell: collisions k_ul n_coll (the
+ * grid's n_coll field) and their detailed-balance inverses at the grid's T,
+ * radiative pumping Gamma_lu and spontaneous plus stimulated emission
+ * A_ul + (g_l/g_u) Gamma_lu, sum of populations = n_mol. gamma: device
+ * double [n_trans][ncell], the radiative pairs ordered by lower then upper
+ * level. pops: device double [ncell][n_lev], written. max_change (host, may
+ * be NULL): max over cells and levels of |n_new - n_old| / n_mol against the
+ * values pops held on entry; when given, the call synchronises `s`.
+ */
+KRL_API krl_status krl_levels_solve(krl_grid* g, const krl_levels_desc* d, const double* gamma, double* pops,
+                                    double* max_change, krl_stream s);
+
+/*
+ * Lambda iteration (Sec. 2.1.3). init_lte != 0: pops starts from
+ * collisional equilibrium (Boltzmann at the grid's T); otherwise from the
+ * values in pops. The emission of every radiative line is frozen at the
+ * starting populations (volume source n_u A_ul, thermal profile). Each of
+ * n_iter cycles, for every line: sets the grid's opacity field to the
+ * current lower-level population, attaches the line (krl_line_set: its own
+ * b, a, sigma0, epsilon, tables), runs packets_per_line packets (ids
+ * distinct per cycle and line, key `seed`), turns the excitation tally into
+ * Gamma; then solves the populations (krl_levels_solve). The grid must have
+ * been created with KRL_OPACITY_NL; its opacity field and line are left as
+ * the last cycle set them. max_change (host [n_iter] or NULL) receives each
+ * cycle's change; the call synchronises `s` once per line and cycle.
+ */
+KRL_API krl_status krl_levels_iterate(krl_grid* g, const krl_levels_desc* d, int n_iter, uint64_t packets_per_line,
+                                      uint64_t seed, int init_lte, double* pops, double* max_change, krl_stream s);
+
 /* ------------------------------------------------------------------ batched models */
 
 typedef struct krl_batch krl_batch;

@@ -72,6 +72,30 @@ class krl_raytrace_desc(C.Structure):
                 ("npix_y", C.c_int), ("fov_cells", C.c_double), ("emiss", C.c_void_p), ("jline", C.c_void_p)]
 
 
+KRL_MAX_LEVELS = 8
+
+
+class krl_levels_desc(C.Structure):
+    _fields_ = [("n_lev", C.c_int), ("E_K", C.c_double * KRL_MAX_LEVELS), ("g", C.c_double * KRL_MAX_LEVELS),
+                ("A", (C.c_double * KRL_MAX_LEVELS) * KRL_MAX_LEVELS),
+                ("k_coll", (C.c_double * KRL_MAX_LEVELS) * KRL_MAX_LEVELS),
+                ("mass_amu", C.c_double), ("n_mol", C.c_void_p)]
+
+
+def levels_desc(E_K, g, A, k_coll, mass_amu, n_mol_tensor) -> krl_levels_desc:
+    """krl_levels_desc from arrays (A[u][l], k_coll[u][l] for u > l)."""
+    d = krl_levels_desc()
+    n = len(E_K)
+    d.n_lev = n
+    for i in range(n):
+        d.E_K[i], d.g[i] = float(E_K[i]), float(g[i])
+        for j in range(n):
+            d.A[i][j], d.k_coll[i][j] = float(A[i][j]), float(k_coll[i][j])
+    d.mass_amu = float(mass_amu)
+    d.n_mol = n_mol_tensor.data_ptr()
+    return d
+
+
 class krl_tune(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("ctas_per_sm", C.c_int),
                 ("refill_min", C.c_int), ("max_iters", C.c_uint64)]
@@ -89,7 +113,7 @@ assert RECORD_DTYPE.itemsize == 20
 EXPORTS = ["krl_last_error", "krl_version", "krl_grid_create", "krl_grid_destroy", "krl_line_set",
            "krl_line_info_get", "krl_run_packets", "krl_tallies_get", "krl_tally_bytes", "krl_tallies_reset",
            "krl_emission_cdf_noalloc", "krl_raytrace_channels", "krl_batch_create", "krl_batch_run",
-           "krl_batch_destroy"]
+           "krl_batch_destroy", "krl_levels_solve", "krl_levels_iterate"]
 
 _lib_handle = None
 
@@ -120,12 +144,16 @@ def load_library(path: str | None = None):
     lib.krl_emission_cdf_noalloc.argtypes = [vp, C.c_int, vp, vp]
     lib.krl_raytrace_channels.argtypes = [vp, C.POINTER(krl_raytrace_desc), vp, vp]
     lib.krl_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
+    lib.krl_levels_solve.argtypes = [vp, C.POINTER(krl_levels_desc), vp, vp, C.POINTER(C.c_double), vp]
+    lib.krl_levels_iterate.argtypes = [vp, C.POINTER(krl_levels_desc), C.c_int, C.c_uint64, C.c_uint64, C.c_int, vp,
+                                       C.POINTER(C.c_double), vp]
     lib.krl_batch_destroy.argtypes = [vp]
     lib.krl_batch_run.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_uint64,
                                   C.POINTER(krl_tune), C.POINTER(krl_run_stats), vp]
     for name in ("krl_grid_create", "krl_grid_destroy", "krl_line_set", "krl_line_info_get",
                  "krl_run_packets", "krl_tallies_get", "krl_tallies_reset", "krl_emission_cdf_noalloc",
-                 "krl_raytrace_channels", "krl_batch_create", "krl_batch_destroy", "krl_batch_run"):
+                 "krl_raytrace_channels", "krl_batch_create", "krl_batch_destroy", "krl_batch_run",
+                 "krl_levels_solve", "krl_levels_iterate"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib_handle = lib
@@ -313,6 +341,21 @@ class Grid:
 
     def reset(self, stream=None):
         krl_tallies_reset(self.handle, stream)
+
+    def levels_solve(self, desc: krl_levels_desc, gamma, pops, stream=None):
+        ch = C.c_double(0.0)
+        _check(load_library().krl_levels_solve(self.handle, C.byref(desc), _ptr(gamma), _ptr(pops), C.byref(ch),
+                                               _stream_handle(stream)))
+        return ch.value
+
+    def levels_iterate(self, desc: krl_levels_desc, n_iter: int, packets_per_line: int, seed: int, pops,
+                       init_lte: bool = True, stream=None):
+        """Lambda iteration; returns the per-cycle population change."""
+        ch = (C.c_double * max(1, n_iter))()
+        _check(load_library().krl_levels_iterate(self.handle, C.byref(desc), int(n_iter), int(packets_per_line),
+                                                 int(seed), int(bool(init_lte)), _ptr(pops), ch,
+                                                 _stream_handle(stream)))
+        return list(ch)[:n_iter]
 
     def raytrace(self, camera: int, npix_x: int, npix_y: int, fov_cells: float, emiss=None, jline=None,
                  theta: float = 0.0, phi: float = 0.0, stream=None):

@@ -53,6 +53,12 @@ struct krl_grid {
     int* bad = nullptr;                       // validation flags
     double* scan_work = nullptr;
     size_t scan_work_n = 0;
+    // level iteration scratch
+    double* lv_gamma = nullptr;          // [kMaxTrans][ncell]
+    double* lv_pops0 = nullptr;          // [ncell][kMaxLevels] frozen emission populations
+    float* lv_rate = nullptr;            // [ncell] source rate of the current line
+    double* lv_total = nullptr;          // [1]
+    unsigned long long* lv_change = nullptr;
 };
 
 namespace {
@@ -358,6 +364,11 @@ krl_status krl_grid_destroy(krl_grid* g)
     dfree(g->opacity);
     for (int k = 0; k < 3; ++k) dfree(g->vel[k]);
     dfree(g->n_coll);
+    dfree(g->lv_gamma);
+    dfree(g->lv_pops0);
+    dfree(g->lv_rate);
+    dfree(g->lv_total);
+    dfree(g->lv_change);
     dfree(g->stats);
     dfree(g->run_stats);
     dfree(g->next);
@@ -725,6 +736,137 @@ krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* 
             stuck += c[ST_STUCK];
         }
         if (stuck) return fail(KRL_ERR_BUDGET, "%llu packets exhausted max_iters", stuck);
+    }
+    return KRL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr double kHPlanck = 6.62607015e-27;
+
+krl_status level_const(const krl_grid* g, const krl_levels_desc* d, LevelConst& L)
+{
+    if (!d || d->n_lev < 2 || d->n_lev > kMaxLevels) return fail(KRL_ERR_ARG, "n_lev must be 2..%d", kMaxLevels);
+    if (!d->n_mol) return fail(KRL_ERR_ARG, "n_mol field is required");
+    L = LevelConst{};
+    L.n = d->n_lev;
+    L.T = g->T_K;
+    for (int i = 0; i < L.n; ++i) {
+        if (!(d->g[i] > 0) || !isfinite(d->E_K[i])) return fail(KRL_ERR_ARG, "bad level %d", i);
+        L.E[i] = d->E_K[i];
+        L.g[i] = d->g[i];
+    }
+    for (int l = 0; l < L.n; ++l)
+        for (int u = l + 1; u < L.n; ++u) {
+            if (d->A[u][l] < 0 || d->k_coll[u][l] < 0) return fail(KRL_ERR_ARG, "negative rate (%d,%d)", u, l);
+            if (d->A[u][l] > 0 && !(d->E_K[u] > d->E_K[l])) return fail(KRL_ERR_ARG, "line (%d,%d) needs E_u > E_l", u, l);
+            L.A[u][l] = d->A[u][l];
+            L.k[u][l] = d->k_coll[u][l];
+            if (d->A[u][l] > 0) {
+                L.tu[L.n_trans] = u;
+                L.tl[L.n_trans] = l;
+                ++L.n_trans;
+            }
+        }
+    return KRL_OK;
+}
+
+krl_status level_scratch(krl_grid* g)
+{
+    const size_t n = (size_t)g->ncell;
+    cudaError_t e = cudaSuccess;
+    if (!g->lv_gamma) e = dalloc(&g->lv_gamma, (size_t)kMaxTrans * n);
+    if (e == cudaSuccess && !g->lv_pops0) e = dalloc(&g->lv_pops0, (size_t)kMaxLevels * n);
+    if (e == cudaSuccess && !g->lv_rate) e = dalloc(&g->lv_rate, n);
+    if (e == cudaSuccess && !g->lv_total) e = dalloc(&g->lv_total, 1);
+    if (e == cudaSuccess && !g->lv_change) e = dalloc(&g->lv_change, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "level scratch");
+    return KRL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+krl_status krl_levels_solve(krl_grid* g, const krl_levels_desc* d, const double* gamma, double* pops,
+                            double* max_change, krl_stream st)
+{
+    cudaStream_t s = (cudaStream_t)st;
+    if (!g || !pops) return fail(KRL_ERR_ARG, "krl_levels_solve: NULL argument");
+    LevelConst L;
+    krl_status ls = level_const(g, d, L);
+    if (ls != KRL_OK) return ls;
+    if (L.n_trans > 0 && !gamma) return fail(KRL_ERR_ARG, "gamma is required when the levels have lines");
+    ls = level_scratch(g);
+    if (ls != KRL_OK) return ls;
+    KRL_CUDA(cudaMemsetAsync(g->lv_change, 0, sizeof(unsigned long long), s), "levels");
+    KRL_CUDA(levels_solve(L, gamma, g->ncell, g->n_coll, d->n_mol, pops, g->lv_change, s), "levels solve");
+    if (max_change) {
+        unsigned long long bits = 0;
+        KRL_CUDA(cudaMemcpyAsync(&bits, g->lv_change, 8, cudaMemcpyDeviceToHost, s), "levels");
+        KRL_CUDA(cudaStreamSynchronize(s), "levels");
+        memcpy(max_change, &bits, 8);
+    }
+    return KRL_OK;
+}
+
+krl_status krl_levels_iterate(krl_grid* g, const krl_levels_desc* d, int n_iter, uint64_t packets_per_line,
+                              uint64_t seed, int init_lte, double* pops, double* max_change, krl_stream st)
+{
+    cudaStream_t s = (cudaStream_t)st;
+    if (!g || !pops) return fail(KRL_ERR_ARG, "krl_levels_iterate: NULL argument");
+    if (n_iter < 0 || packets_per_line == 0) return fail(KRL_ERR_ARG, "need n_iter >= 0 and packets_per_line > 0");
+    if (g->opacity_kind != KRL_OPACITY_NL) return fail(KRL_ERR_ARG, "the grid must take its opacity as n_l");
+    LevelConst L;
+    krl_status ls = level_const(g, d, L);
+    if (ls != KRL_OK) return ls;
+    ls = level_scratch(g);
+    if (ls != KRL_OK) return ls;
+    const int ncell = g->ncell;
+    const size_t n = (size_t)ncell;
+    if (init_lte) KRL_CUDA(levels_lte(L, d->n_mol, ncell, pops, s), "levels lte");
+    KRL_CUDA(cudaMemcpyAsync(g->lv_pops0, pops, n * L.n * sizeof(double), cudaMemcpyDeviceToDevice, s), "levels");
+    for (int it = 0; it < n_iter; ++it) {
+        for (int t = 0; t < L.n_trans; ++t) {
+            const int u = L.tu[t], l = L.tl[t];
+            KRL_CUDA(levels_field(pops, ncell, L.n, l, 1.0, g->opacity, s), "lower-level field");
+            KRL_CUDA(levels_field(g->lv_pops0, ncell, L.n, u, L.A[u][l], g->lv_rate, s), "frozen emission");
+            KRL_CUDA(levels_sum_rate(g->lv_pops0, ncell, L.n, u, L.A[u][l], g->lv_total, s), "emission total");
+            krl_line_desc ld{};
+            ld.nu0_hz = (L.E[u] - L.E[l]) * kKB / kHPlanck;
+            ld.mass_amu = d->mass_amu;
+            ld.A_ul = L.A[u][l];
+            ld.g_u = L.g[u];
+            ld.g_l = L.g[l];
+            ld.k_ul = L.k[u][l];
+            ld.src_kind = KRL_SRC_VOLUME;
+            ld.src_profile = KRL_PROFILE_GAUSSIAN;
+            ld.src_rate = g->lv_rate;
+            ld.band_axis = -1;
+            ld.luminosity = 1.0;
+            ld.spec_xmin = -40.0;
+            ld.spec_xmax = 40.0;
+            ld.spec_nbins = 80;
+            ld.tally_flags = KRL_TALLY_EXC;
+            krl_status rs = krl_line_set(g, &ld, st);
+            if (rs != KRL_OK) return rs;
+            const uint64_t first = ((uint64_t)it * L.n_trans + t) * packets_per_line;
+            rs = krl_run_packets(g, packets_per_line, first, seed, nullptr, nullptr, nullptr, st);
+            if (rs != KRL_OK) return rs;
+            KRL_CUDA(levels_gamma(g->exc, ncell, g->lv_total, g->cell_cm, g->info.sigma0_cm2, (double)packets_per_line,
+                                  g->lv_gamma + (size_t)t * n, s),
+                     "gamma");
+        }
+        KRL_CUDA(cudaMemsetAsync(g->lv_change, 0, sizeof(unsigned long long), s), "levels");
+        KRL_CUDA(levels_solve(L, g->lv_gamma, ncell, g->n_coll, d->n_mol, pops, g->lv_change, s), "levels solve");
+        if (max_change) {
+            unsigned long long bits = 0;
+            KRL_CUDA(cudaMemcpyAsync(&bits, g->lv_change, 8, cudaMemcpyDeviceToHost, s), "levels");
+            KRL_CUDA(cudaStreamSynchronize(s), "levels");
+            memcpy(max_change + it, &bits, 8);
+        }
     }
     return KRL_OK;
 }

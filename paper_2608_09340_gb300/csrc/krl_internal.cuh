@@ -130,6 +130,27 @@ struct RayArgs {
 };
 cudaError_t launch_raytrace(const RayArgs& A, cudaStream_t s);
 
+// ---------------------------------------------------------------- statistical equilibrium (levels.cu)
+constexpr int kMaxLevels = KRL_MAX_LEVELS;
+constexpr int kMaxTrans = kMaxLevels * (kMaxLevels - 1) / 2;
+struct LevelConst {
+    int n;                              // levels
+    double T;                           // gas temperature [K]
+    double E[kMaxLevels];               // energies / k_B [K]
+    double g[kMaxLevels];
+    double A[kMaxLevels][kMaxLevels];   // A[u][l], u > l
+    double k[kMaxLevels][kMaxLevels];   // k_coll[u][l], u > l
+    int n_trans;                        // radiative pairs, ordered by (l, u)
+    int tu[kMaxTrans], tl[kMaxTrans];
+};
+cudaError_t levels_lte(const LevelConst& L, const float* n_mol, int ncell, double* pops, cudaStream_t s);
+cudaError_t levels_field(const double* pops, int ncell, int n_lev, int lev, double scale, float* out, cudaStream_t s);
+cudaError_t levels_sum_rate(const double* pops, int ncell, int n_lev, int u, double A, double* total, cudaStream_t s);
+cudaError_t levels_gamma(const double* exc, int ncell, const double* total, double dx, double sigma0, double n_packets,
+                         double* gamma, cudaStream_t s);
+cudaError_t levels_solve(const LevelConst& L, const double* gamma, int ncell, const float* n_coll, const float* n_mol,
+                         double* pops, unsigned long long* max_change, cudaStream_t s);
+
 // ---------------------------------------------------------------- setup kernels (tables.cu)
 struct LineTables {
     float* voigt_lnH;   // [kVoigtN]

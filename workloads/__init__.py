@@ -240,6 +240,59 @@ def envelope(n: int = 64, n_ch: int = 16, n_packets: int = 100_000, seed: int = 
         tallies=("exc", "J", "emiss"), n_packets=n_packets, seed=seed)
 
 
+def gaussian_field(shape, slope: float, rng) -> np.ndarray:
+    """Periodic Gaussian random field with 3-D power spectrum P(k) ~ k^slope,
+    zero mean and unit variance (white noise shaped in Fourier space)."""
+    nz, ny, nx = shape
+    kz = np.fft.fftfreq(nz)[:, None, None]
+    ky = np.fft.fftfreq(ny)[None, :, None]
+    kx = np.fft.rfftfreq(nx)[None, None, :]
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(k)
+    amp[k > 0] = k[k > 0] ** (slope / 2.0)
+    f = np.fft.irfftn(np.fft.rfftn(rng.normal(size=shape)) * amp, s=shape, axes=(0, 1, 2))
+    return (f - f.mean()) / f.std()
+
+
+@dataclasses.dataclass
+class LevelSpec:
+    """Levels of a linear rotor for the statistical-equilibrium workloads."""
+    n_lev: int = 5
+    B_K: float = 2.77            # E_J = B J (J + 1)
+    A1: float = 1e-7             # A_{J -> J-1} = A1 J^3
+    k_ul: float = 1e-11          # collisional de-excitation, every pair u > l
+    mass_amu: float = 28.0
+
+
+def cloud(n: int = 128, seed: int = 3, mean_n: float = 1e3, sigma_lnrho: float = 1.5, T_K: float = 20.0,
+          sigma_v_kms: float = 1.0, abundance: float = 1e-4, box_pc: float = 0.04,
+          packets_per_line: int = 10_000_000):
+    """Non-LTE molecular cloud: log-normal density (ln rho a Gaussian random
+    field with P(k) ~ k^-11/3, sigma_lnrho = 1.5, mean n = 1e3 cm^-3 exactly),
+    each velocity component a Gaussian random field with P(k) ~ k^-4 and a
+    1-D dispersion of exactly 1 km/s, T = 20 K, emitter abundance 1e-4, a
+    5-level rotor. Returns (Problem, n_mol [nz,ny,nx], LevelSpec); the
+    Problem's opacity and source are placeholders that the level iteration
+    replaces line by line."""
+    rng = np.random.default_rng(seed)
+    shape = (n, n, n)
+    lnrho = sigma_lnrho * gaussian_field(shape, -11.0 / 3.0, rng)
+    rho = np.exp(lnrho)
+    dens = mean_n * rho / rho.mean()
+    vel = np.stack([sigma_v_kms * 1e5 * gaussian_field(shape, -4.0, rng) for _ in range(3)])
+    n_mol = (abundance * dens).astype(np.float32)
+    pc = 3.0856775814913673e18
+    spec = LevelSpec()
+    p = Problem(
+        name=f"cloud{n}", shape=shape, cell_cm=box_pc * pc / n, periodic=(False, False, False),
+        opacity_kind="n_l", opacity=n_mol.copy(), T_K=T_K,
+        line=Line(115.27e9, spec.mass_amu, spec.A1, 3.0, 1.0, spec.k_ul, 0.0),
+        source=Source(SOURCE_VOLUME, profile=PROFILE_GAUSSIAN, rate=n_mol.copy()),
+        vel_cms=vel.astype(np.float32), n_coll=dens.astype(np.float32),
+        spectrum=(-20.0, 20.0, 80), tallies=("exc",), n_packets=packets_per_line, seed=seed)
+    return p, n_mol, spec
+
+
 def model_set(n_models: int = 64, total_packets: int = 10_000_000, seed: int = 4,
               sides=(32, 48, 64, 96, 128), tau_range=(1e3, 1e7), a_range=(1e-4, 1e-2),
               vmax_kms=300.0, T_K: float = 1e4):
