@@ -38,7 +38,7 @@ UNIT = "scatterings/s"
 OPS_PER_SCAT = 330
 OPS_PER_CROSS = 50
 FP32_LANES_PER_SM = 128
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "transport_sphere64_tau1e6.txt")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "transport_sphere64_tau3e4.txt")
 KERNEL_SRC = os.path.join(ROOT, "paper_2608_09340_gb300", "csrc", "transport.cu")
 
 
