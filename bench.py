@@ -6,8 +6,8 @@ One step = one krl_run_packets launch over the next PACKETS_PER_STEP packet
 ids of the 1e6-packet job (every step of the pass runs: emission, cell walk,
 scattering, tallies, escape, regeneration, counter reduction). Inputs are
 resident on the device; L2 is flushed (a 256 MiB write) before every timed
-step. Steps alternate between two streams so that one step's tail overlaps
-the next step's start (--serial: one stream); the K steps are bracketed by
+step. Steps rotate over --streams streams (default 2) so that one step's
+tail overlaps the next step's start (--serial: one stream); the K steps are bracketed by
 CUDA events, and every launch also by its own pair on its stream.
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
@@ -55,8 +55,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-raytrace", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--serial", dest="pipeline", action="store_false",
-                    help="issue every step on one stream (no overlap of one step's tail with the next)")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="streams the steps rotate over (1: no overlap of one step's tail with the next)")
+    ap.add_argument("--serial", dest="streams", action="store_const", const=1,
+                    help="same as --streams 1")
     return ap.parse_args()
 
 
@@ -329,12 +331,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # Steps are issued alternately on two streams: a step's launch starts on
+    # Steps are issued round robin on several streams: a step's launch starts on
     # the SMs that the previous step's tail (its last, longest packets) has
     # already released, as a production job streams its batches. Each stream
     # flushes L2 (its own 256 MiB write) before each of its steps.
-    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
-    flushes = [flush, torch.empty(256 << 20, dtype=torch.uint8, device=dev)]
+    nstr = max(1, args.streams)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nstr)]
+    flushes = [flush] + [torch.empty(256 << 20, dtype=torch.uint8, device=dev) for _ in range(nstr - 1)]
     step_id = 0
     for _ in range(args.warmup):
         lo, n = shard.step_range(step_id, rank, world, B)
@@ -352,9 +355,9 @@ def main():
     for st_ in streams:
         st_.wait_stream(stream)
     for k in range(args.steps):
-        sk = streams[k % 2 if args.pipeline else 0]
+        sk = streams[k % nstr]
         with torch.cuda.stream(sk):
-            flushes[k % 2].zero_()
+            flushes[k % nstr].zero_()
             lo, n = shard.step_range(step_id, rank, world, B)
             ev[k][0].record(sk)
             g.run(n=n, first=lo, want_stats=False, stream=sk)
@@ -440,7 +443,7 @@ def main():
                        "T_K": 1e4, "source": "central point, line centre", "packets_per_step": B,
                        "job_packets": JOB_PACKETS, "scatterings_per_packet": scat_all / max(pk_all, 1),
                        "l2": "flushed before every timed step (256 MiB write)",
-                       "steps_issue": "two streams, alternating" if args.pipeline else "one stream",
+                       "steps_issue": f"{nstr} streams, round robin" if nstr > 1 else "one stream",
                        "parallelism": f"packet-id shards x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "raytrace": rt, "batch": bt,
             "gpu_launches": 2 * args.steps, "wall_s_timed": wall,

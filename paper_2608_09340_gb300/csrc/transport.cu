@@ -76,14 +76,25 @@ struct Ops;
 
 template <>
 struct Ops<float> {
-    static __device__ __forceinline__ float uni(uint32_t r) { return (float)(r >> 9) * 0x1p-23f + 0x1p-24f; }
+    // ((r >> 9) + 1/2) 2^-23 without an int-to-float conversion: the bits
+    // give 1 + (r >> 9) 2^-23, and subtracting 1 - 2^-24 is exact (Sterbenz)
+    static __device__ __forceinline__ float uni(uint32_t r)
+    {
+        return __uint_as_float((r >> 9) + 0x3f800000u) - 0x1.fffffep-1f;
+    }
     static __device__ __forceinline__ float ln(float v) { return __logf(v); }
     static __device__ __forceinline__ float lg10(float v) { return __log2f(v) * 0.30102999566398120f; }
     static __device__ __forceinline__ float ex(float v) { return __expf(v); }
     // sqrt(v) for v >= 0 as v * rsqrt(v) (one MUFU op, 2 ulp)
     static __device__ __forceinline__ float sq(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
     static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    // 1/a to about 1 ulp (one MUFU op; used for the exit distances only)
+    static __device__ __forceinline__ float rcp(float a)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
     // sin and cos of 2 pi u for u in (0, 1): shift to [-pi, pi] where the
     // hardware approximation is accurate, then reflect.
     static __device__ __forceinline__ void sc2pi(float u, float* s, float* c)
@@ -479,18 +490,262 @@ __device__ __forceinline__ T warp_sum(T v)
 template <typename R, unsigned F>
 constexpr int max_block() { return (sizeof(R) == 4 && !(F & F_RICH)) ? 512 : 256; }
 
+// Per-lane event counters (summed over the CTA at the end of a model).
+struct LaneStats {
+    unsigned long long emit, esc, des, stuck, scat, cross;
+};
+
+// ---------------------------------------------------------------- tail compaction
+//
+// Dynamic shared memory after the tables: a control block (the CTA's "ids
+// ran out" flag and per-warp packet counts, double-buffered by round) and a
+// stash that holds one packet per thread, field-major (one 32-bit word per
+// field and slot, so consecutive slots fall in consecutive banks).
+constexpr size_t kCtlOff = (kSmemBytes + 15) / 16 * 16;
+constexpr int kCtlInts = 4 + 2 * 32;
+constexpr size_t kStashOff = kCtlOff + (size_t)kCtlInts * sizeof(int);
+// Events a lane runs between two compaction checks in the tail.
+constexpr int kTailRound = 32;
+
+// Words per stashed packet: cell (c, cx, cy, cz), nscat, ncross, cell0, id
+// (2 words), and px, py, pz, nx, ny, nz, x, tau in R.
+template <typename R>
+constexpr int stash_words() { return 9 + 8 * (int)(sizeof(R) / 4); }
+
+template <typename R, unsigned F>
+constexpr size_t smem_bytes(int block) { return kStashOff + (size_t)stash_words<R>() * 4u * (size_t)block; }
+
+template <typename R>
+__device__ __forceinline__ void put_r(uint32_t* w, int& f, int n, int slot, R v)
+{
+    if constexpr (sizeof(R) == 4) {
+        w[(f++) * n + slot] = __float_as_uint(v);
+    } else {
+        w[(f++) * n + slot] = (uint32_t)__double2loint(v);
+        w[(f++) * n + slot] = (uint32_t)__double2hiint(v);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R get_r(const uint32_t* w, int& f, int n, int slot)
+{
+    if constexpr (sizeof(R) == 4) {
+        return __uint_as_float(w[(f++) * n + slot]);
+    } else {
+        const uint32_t lo = w[(f++) * n + slot];
+        const uint32_t hi = w[(f++) * n + slot];
+        return __hiloint2double((int)hi, (int)lo);
+    }
+}
+
+// Moves a packet into / out of stash slot `slot`. The visit tallies are
+// flushed before (they belong to the cell visit, not the packet), and the
+// derived fields (1/n, the cell record) are recomputed from the stored ones
+// by the same functions, so a restored packet continues bit for bit as it
+// would have in its old lane.
+template <typename R>
+__device__ __forceinline__ void stash_put(uint32_t* w, int n, int slot, const Pkt<R>& p)
+{
+    int f = 0;
+    w[(f++) * n + slot] = (uint32_t)p.c;
+    w[(f++) * n + slot] = (uint32_t)p.cx;
+    w[(f++) * n + slot] = (uint32_t)p.cy;
+    w[(f++) * n + slot] = (uint32_t)p.cz;
+    w[(f++) * n + slot] = p.nscat;
+    w[(f++) * n + slot] = p.ncross;
+    w[(f++) * n + slot] = p.cell0;
+    w[(f++) * n + slot] = (uint32_t)p.id;
+    w[(f++) * n + slot] = (uint32_t)(p.id >> 32);
+    put_r<R>(w, f, n, slot, p.px);
+    put_r<R>(w, f, n, slot, p.py);
+    put_r<R>(w, f, n, slot, p.pz);
+    put_r<R>(w, f, n, slot, p.nx);
+    put_r<R>(w, f, n, slot, p.ny);
+    put_r<R>(w, f, n, slot, p.nz);
+    put_r<R>(w, f, n, slot, p.x);
+    put_r<R>(w, f, n, slot, p.tau);
+}
+
+template <typename R>
+__device__ __forceinline__ void stash_get(const TransportArgs& A, const uint32_t* w, int n, int slot, Pkt<R>& p)
+{
+    int f = 0;
+    p.c = (int)w[(f++) * n + slot];
+    p.cx = (int)w[(f++) * n + slot];
+    p.cy = (int)w[(f++) * n + slot];
+    p.cz = (int)w[(f++) * n + slot];
+    p.nscat = w[(f++) * n + slot];
+    p.ncross = w[(f++) * n + slot];
+    p.cell0 = w[(f++) * n + slot];
+    const uint32_t lo = w[(f++) * n + slot];
+    const uint32_t hi = w[(f++) * n + slot];
+    p.id = ((unsigned long long)hi << 32) | lo;
+    p.px = get_r<R>(w, f, n, slot);
+    p.py = get_r<R>(w, f, n, slot);
+    p.pz = get_r<R>(w, f, n, slot);
+    const R nx = get_r<R>(w, f, n, slot);
+    const R ny = get_r<R>(w, f, n, slot);
+    const R nz = get_r<R>(w, f, n, slot);
+    set_dir(p, nx, ny, nz);
+    p.x = get_r<R>(w, f, n, slot);
+    p.tau = get_r<R>(w, f, n, slot);
+    p.rec = __ldg(A.cells + p.c);
+    p.vis_scat = 0;
+    p.vis_exc = (R)0;
+    p.prev_scat = true;
+}
+
+// ---------------------------------------------------------------- one event
+
+// Advances an active packet by one event in its current cell (a scattering
+// inside the cell or a crossing of the nearest face). Returns false when the
+// packet has ended (escape, destruction or event budget).
+template <typename R, unsigned F>
+__device__ __forceinline__ bool advance(const TransportArgs& A, Pkt<R>& p, const float* sv, const float* sx,
+                                        const float* sc, const unsigned char* sg, R a, R H0, LaneStats& st)
+{
+    using O = Ops<R>;
+    if ((unsigned long long)p.nscat + p.ncross >= A.max_iters) {
+        flush_visit<R, F>(A, p);
+        ++st.stuck;
+        st.scat += p.nscat;
+        st.cross += p.ncross;
+        write_record(A, p, 3);
+        return false;
+    }
+    // Draw the next scattering's random numbers before the profile lookup
+    // when the last event was a scattering (the common case deep in the
+    // line core): the two Philox chains overlap the lookup's latency.
+    const uint32_t idlo = (uint32_t)p.id, idhi = (uint32_t)(p.id >> 32);
+    Words w0 = {{0u, 0u, 0u, 0u}}, w1 = {{0u, 0u, 0u, 0u}};
+    const bool spec = p.prev_scat;
+    if (spec) {
+        w0 = philox(idlo, idhi, p.nscat + 1u, 0u, A.k0, A.k1);
+        w1 = philox(idlo, idhi, p.nscat + 1u, 1u, A.k0, A.k1);
+    }
+    const R vdn = (F & F_VEL) ? vdot<R>(p.nx, p.ny, p.nz, p.rec) : (R)0;
+    const R xcom = p.x - vdn;
+    const R H = voigt<R>(xcom, sv, a, H0);
+    const R alpha = (R)p.rec.x * H;
+    const R BIG = O::big();
+    R tx = p.nx > (R)0 ? ((R)1 - p.px) * p.ix : (p.nx < (R)0 ? -p.px * p.ix : BIG);
+    R ty = p.ny > (R)0 ? ((R)1 - p.py) * p.iy : (p.ny < (R)0 ? -p.py * p.iy : BIG);
+    R tz = p.nz > (R)0 ? ((R)1 - p.pz) * p.iz : (p.nz < (R)0 ? -p.pz * p.iz : BIG);
+    R sx_ = tx;
+    int axis = 0;
+    if (ty < sx_) { sx_ = ty; axis = 1; }
+    if (tz < sx_) { sx_ = tz; axis = 2; }
+    const bool scat = p.tau < alpha * sx_;
+    const R ds = scat ? O::dv(p.tau, alpha) : sx_;
+    p.px = fmin((R)1, fmax((R)0, p.px + ds * p.nx));
+    p.py = fmin((R)1, fmax((R)0, p.py + ds * p.ny));
+    p.pz = fmin((R)1, fmax((R)0, p.pz + ds * p.nz));
+    if (F & F_RICH) {
+        if (A.rich & KRL_TALLY_EXC) p.vis_exc += ds * H;
+        if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H);
+    }
+    p.prev_scat = scat;
+    if (scat) {
+        // ---- scattering (event e = nscat): block 0 = {u_par, bm_r, bm_phi, tau},
+        //      block 1 = {mu, phi, eps_test, -}
+        ++p.nscat;
+        ++p.vis_scat;
+        if (!spec) {
+            w0 = philox(idlo, idhi, p.nscat, 0u, A.k0, A.k1);
+            w1 = philox(idlo, idhi, p.nscat, 1u, A.k0, A.k1);
+        }
+        if ((F & F_RICH) && (A.rich & kRichEps)) {
+            if (O::uni(w1.w[2]) < (R)__ldg(A.eps + p.c)) {
+                flush_visit<R, F>(A, p);
+                ++st.des;
+                st.scat += p.nscat;
+                st.cross += p.ncross;
+                write_record(A, p, 2);
+                return false;
+            }
+        }
+        // independent long-latency work first: Box-Muller, new direction,
+        // the sampler's logs; then the table walk
+        R bs, bc;
+        O::sc2pi(O::uni(w0.w[2]), &bs, &bc);
+        const R rad = O::sq(fmax((R)0, -O::ln(O::uni(w0.w[1]))));
+        R mx, my, mz;
+        iso_dir<R>(O::uni(w1.w[0]), O::uni(w1.w[1]), mx, my, mz);
+        R L;
+        const int gm = us_bin<R>(O::uni(w0.w[0]), L);
+        const R tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
+        const R z1 = rad * bc, z2 = rad * bs;
+        const R upar = fabs(xcom) > (R)300 ? z2 : us_sample<R>(xcom, L, gm, sx, sc, sg);
+        const R g = p.nx * mx + p.ny * my + p.nz * mz;
+        const R sg_ = O::sq(fmax((R)0, (R)1 - g * g));
+        const R xout = xcom + upar * (g - (R)1) + z1 * sg_;
+        set_dir(p, mx, my, mz);
+        const R vdo = (F & F_VEL) ? vdot<R>(mx, my, mz, p.rec) : (R)0;
+        p.x = xout + vdo;
+        p.tau = tau_new;
+        return true;
+    }
+    // ---- cross the face on `axis`
+    p.tau -= alpha * sx_;
+    ++p.ncross;
+    flush_visit<R, F>(A, p);
+    const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
+    const int stride = axis == 0 ? 1 : (axis == 1 ? A.nx : A.nx * A.ny);
+    const int cur = axis == 0 ? p.cx : (axis == 1 ? p.cy : p.cz);
+    const R nd = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+    const int step = nd > (R)0 ? 1 : -1;
+    int nc = cur + step;
+    int dc = step * stride;
+    const R pnew = step > 0 ? (R)0 : (R)1;
+    if (axis == 0) p.px = pnew;
+    else if (axis == 1) p.py = pnew;
+    else p.pz = pnew;
+    if (nc < 0 || nc >= dim) {
+        if (!((A.periodic >> axis) & 1u)) {
+            spectrum_add(A, (double)p.x);
+            ++st.esc;
+            st.scat += p.nscat;
+            st.cross += p.ncross;
+            write_record(A, p, 1);
+            return false;
+        }
+        if (nc < 0) { nc += dim; dc += dim * stride; }
+        else { nc -= dim; dc -= dim * stride; }
+    }
+    if (axis == 0) p.cx = nc;
+    else if (axis == 1) p.cy = nc;
+    else p.cz = nc;
+    p.c += dc;
+    p.rec = __ldg(A.cells + p.c);
+    return true;
+}
+
 // One model's walk by the whole CTA: stage the model's tables in shared
 // memory, run packets until the model's id counter is exhausted and every
 // lane has finished, then add the counters. Every thread of the CTA calls it.
+//
+// Bulk phase: each lane owns a packet; a warp refills its idle lanes with one
+// atomic on the id counter (ballot + popc + shuffle). The first warp of the
+// CTA that finds the counter exhausted raises a CTA flag, and every warp
+// leaves the bulk phase at its next iteration.
+//
+// Tail phase (the remaining, typically longest packets): rounds of
+// kTailRound events per lane; after each round the CTA counts its running
+// packets and, if they occupy more warps than they would fill, moves them
+// (through the shared-memory stash) to the lowest threads. Emptied warps
+// then wait at the round barrier without issuing, so the surviving packets
+// run in full warps instead of sharing the issue slots with idle lanes.
 template <typename R, unsigned F>
 __device__ __forceinline__ void run_model(const TransportArgs& A, float* sm)
 {
-    using O = Ops<R>;
+    int* ctl = reinterpret_cast<int*>(reinterpret_cast<char*>(sm) + kCtlOff);
+    uint32_t* stash = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + kStashOff);
     for (int i = threadIdx.x; i < kVoigtN; i += blockDim.x) sm[kSmemVoigt + i] = A.voigt_lnH[i];
     for (int i = threadIdx.x; i < kUsNx; i += blockDim.x) sm[kSmemUsX + i] = A.us_x[i];
     for (int i = threadIdx.x; i < kUsNx * kUsNu; i += blockDim.x) sm[kSmemUsC + i] = A.us_lncdf[i];
     unsigned char* sgw = reinterpret_cast<unsigned char*>(sm + kSmemFloats);
     for (int i = threadIdx.x; i < kUsNx * kGuideN; i += blockDim.x) sgw[i] = A.us_guide[i];
+    if (threadIdx.x == 0) ctl[0] = 0;
     __syncthreads();
     const float* sv = sm + kSmemVoigt;
     const float* sx = sm + kSmemUsX;
@@ -500,165 +755,83 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, float* sm)
     const R a = (R)A.a;
     const R H0 = (R)__ldg(A.H0);
     const unsigned lane = threadIdx.x & 31u;
+    const int warp = (int)(threadIdx.x >> 5);
+    const int nwarps = (int)(blockDim.x >> 5);
     Pkt<R> p;
     bool active = false;
-    bool exhausted = false;
-    unsigned long long st_emit = 0, st_esc = 0, st_des = 0, st_stuck = 0, st_scat = 0, st_cross = 0;
+    LaneStats st = {0, 0, 0, 0, 0, 0};
 
+    // Both phases run in one loop so that the event code is inlined once.
+    const int n = (int)blockDim.x;
+    bool bulk = true;
+    int round = 0, it = 0;
     for (;;) {
-        // ---- warp-level refill: one atomic per warp, ids compacted into idle lanes
-        if (!exhausted) {
-            unsigned idle = __ballot_sync(kFull, !active);
-            int nidle = __popc(idle);
-            if (nidle == 32 || nidle >= A.refill_min) {
+        if (bulk) {
+            // ---- bulk phase: refill idle lanes, leave when the ids run out
+            const unsigned idle = __ballot_sync(kFull, !active);
+            const int nidle = __popc(idle);
+            int stop = 0;
+            if (lane == 0) stop = *reinterpret_cast<volatile int*>(ctl);
+            bool leave = __shfl_sync(kFull, stop, 0) != 0;
+            if (!leave && (nidle == 32 || (nidle > 0 && nidle >= A.refill_min))) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(A.next, (unsigned long long)nidle);
                 base = __shfl_sync(kFull, base, 0);
-                if (base + (unsigned long long)nidle >= A.n) exhausted = true;
+                leave = base + (unsigned long long)nidle >= A.n;
+                if (leave && lane == 0) *reinterpret_cast<volatile int*>(ctl) = 1;
                 if (!active) {
-                    unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
+                    const unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
                     if (k < A.n) {
                         p.id = A.first + k;
-                        ++st_emit;
+                        ++st.emit;
                         if (emit<R, F>(A, p)) {
                             active = true;
                         } else {
                             spectrum_add(A, (double)p.x);
-                            ++st_esc;
+                            ++st.esc;
                             write_record(A, p, 1);
                         }
                     }
                 }
             }
-        }
-        // Once the warp knows that no ids remain (a warp-uniform fact), idle
-        // lanes leave and active lanes finish their packets with no further
-        // warp-wide votes; until then every lane comes back to the ballot.
-        if (!active) {
-            if (exhausted) break;
-            continue;
-        }
-
-        // ---- one event in the current cell
-        if ((unsigned long long)p.nscat + p.ncross >= A.max_iters) {
-            flush_visit<R, F>(A, p);
-            ++st_stuck;
-            st_scat += p.nscat;
-            st_cross += p.ncross;
-            write_record(A, p, 3);
-            active = false;
-            continue;
-        }
-        // Draw the next scattering's random numbers before the profile lookup
-        // when the last event was a scattering (the common case deep in the
-        // line core): the two Philox chains overlap the lookup's latency.
-        const uint32_t idlo = (uint32_t)p.id, idhi = (uint32_t)(p.id >> 32);
-        Words w0 = {{0u, 0u, 0u, 0u}}, w1 = {{0u, 0u, 0u, 0u}};
-        const bool spec = p.prev_scat;
-        if (spec) {
-            w0 = philox(idlo, idhi, p.nscat + 1u, 0u, A.k0, A.k1);
-            w1 = philox(idlo, idhi, p.nscat + 1u, 1u, A.k0, A.k1);
-        }
-        const R vdn = (F & F_VEL) ? vdot<R>(p.nx, p.ny, p.nz, p.rec) : (R)0;
-        const R xcom = p.x - vdn;
-        const R H = voigt<R>(xcom, sv, a, H0);
-        const R alpha = (R)p.rec.x * H;
-        const R BIG = O::big();
-        R tx = p.nx > (R)0 ? ((R)1 - p.px) * p.ix : (p.nx < (R)0 ? -p.px * p.ix : BIG);
-        R ty = p.ny > (R)0 ? ((R)1 - p.py) * p.iy : (p.ny < (R)0 ? -p.py * p.iy : BIG);
-        R tz = p.nz > (R)0 ? ((R)1 - p.pz) * p.iz : (p.nz < (R)0 ? -p.pz * p.iz : BIG);
-        R sx_ = tx;
-        int axis = 0;
-        if (ty < sx_) { sx_ = ty; axis = 1; }
-        if (tz < sx_) { sx_ = tz; axis = 2; }
-        const bool scat = p.tau < alpha * sx_;
-        const R ds = scat ? O::dv(p.tau, alpha) : sx_;
-        p.px = fmin((R)1, fmax((R)0, p.px + ds * p.nx));
-        p.py = fmin((R)1, fmax((R)0, p.py + ds * p.ny));
-        p.pz = fmin((R)1, fmax((R)0, p.pz + ds * p.nz));
-        if (F & F_RICH) {
-            if (A.rich & KRL_TALLY_EXC) p.vis_exc += ds * H;
-            if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H);
-        }
-        p.prev_scat = scat;
-        if (scat) {
-            // ---- scattering (event e = nscat): block 0 = {u_par, bm_r, bm_phi, tau},
-            //      block 1 = {mu, phi, eps_test, -}
-            ++p.nscat;
-            ++p.vis_scat;
-            if (!spec) {
-                w0 = philox(idlo, idhi, p.nscat, 0u, A.k0, A.k1);
-                w1 = philox(idlo, idhi, p.nscat, 1u, A.k0, A.k1);
+            if (leave) {                      // warp-uniform; once per warp
+                bulk = false;
+                __syncthreads();
             }
-            if ((F & F_RICH) && (A.rich & kRichEps)) {
-                if (O::uni(w1.w[2]) < (R)__ldg(A.eps + p.c)) {
+        } else if (it == kTailRound || !__any_sync(kFull, active)) {
+            // ---- tail phase, end of a round: count and compact
+            const unsigned m = __ballot_sync(kFull, active);
+            int* cnt = ctl + 4 + 32 * (round & 1);
+            if (lane == 0) cnt[warp] = __popc(m);
+            __syncthreads();
+            int total = 0, before = 0, busy = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                const int c = cnt[w];
+                total += c;
+                before += w < warp ? c : 0;
+                busy += c > 0 ? 1 : 0;
+            }
+            if (total == 0) break;            // CTA-uniform
+            if (busy > (total + 31) / 32) {   // CTA-uniform
+                if (active) {
                     flush_visit<R, F>(A, p);
-                    ++st_des;
-                    st_scat += p.nscat;
-                    st_cross += p.ncross;
-                    write_record(A, p, 2);
-                    active = false;
-                    continue;
+                    stash_put<R>(stash, n, before + __popc(m & ((1u << lane) - 1u)), p);
                 }
+                __syncthreads();
+                // the stash is next written after a later round's count
+                // barrier, which every thread reaches only after this read
+                active = (int)threadIdx.x < total;
+                if (active) stash_get<R>(A, stash, n, (int)threadIdx.x, p);
             }
-            // independent long-latency work first: Box-Muller, new direction,
-            // the sampler's logs; then the table walk
-            R bs, bc;
-            O::sc2pi(O::uni(w0.w[2]), &bs, &bc);
-            const R rad = O::sq(fmax((R)0, -O::ln(O::uni(w0.w[1]))));
-            R mx, my, mz;
-            iso_dir<R>(O::uni(w1.w[0]), O::uni(w1.w[1]), mx, my, mz);
-            R L;
-            const int gm = us_bin<R>(O::uni(w0.w[0]), L);
-            const R tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
-            const R z1 = rad * bc, z2 = rad * bs;
-            const R upar = fabs(xcom) > (R)300 ? z2 : us_sample<R>(xcom, L, gm, sx, sc, sg);
-            const R g = p.nx * mx + p.ny * my + p.nz * mz;
-            const R sg_ = O::sq(fmax((R)0, (R)1 - g * g));
-            const R xout = xcom + upar * (g - (R)1) + z1 * sg_;
-            set_dir(p, mx, my, mz);
-            const R vdo = (F & F_VEL) ? vdot<R>(mx, my, mz, p.rec) : (R)0;
-            p.x = xout + vdo;
-            p.tau = tau_new;
-        } else {
-            // ---- cross the face on `axis`
-            p.tau -= alpha * sx_;
-            ++p.ncross;
-            flush_visit<R, F>(A, p);
-            const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
-            const int stride = axis == 0 ? 1 : (axis == 1 ? A.nx : A.nx * A.ny);
-            const int cur = axis == 0 ? p.cx : (axis == 1 ? p.cy : p.cz);
-            const R nd = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
-            const int step = nd > (R)0 ? 1 : -1;
-            int nc = cur + step;
-            int dc = step * stride;
-            const R pnew = step > 0 ? (R)0 : (R)1;
-            if (axis == 0) p.px = pnew;
-            else if (axis == 1) p.py = pnew;
-            else p.pz = pnew;
-            if (nc < 0 || nc >= dim) {
-                if (!((A.periodic >> axis) & 1u)) {
-                    spectrum_add(A, (double)p.x);
-                    ++st_esc;
-                    st_scat += p.nscat;
-                    st_cross += p.ncross;
-                    write_record(A, p, 1);
-                    active = false;
-                    continue;
-                }
-                if (nc < 0) { nc += dim; dc += dim * stride; }
-                else { nc -= dim; dc -= dim * stride; }
-            }
-            if (axis == 0) p.cx = nc;
-            else if (axis == 1) p.cy = nc;
-            else p.cz = nc;
-            p.c += dc;
-            p.rec = __ldg(A.cells + p.c);
+            ++round;
+            it = 0;
         }
+        if (!bulk) ++it;
+        if (active) active = advance<R, F>(A, p, sv, sx, sc, sg, a, H0, st);
     }
 
-    const unsigned long long tot[6] = {warp_sum(st_emit), warp_sum(st_esc), warp_sum(st_des),
-                                       warp_sum(st_stuck), warp_sum(st_scat), warp_sum(st_cross)};
+    const unsigned long long tot[6] = {warp_sum(st.emit), warp_sum(st.esc),  warp_sum(st.des),
+                                       warp_sum(st.stuck), warp_sum(st.scat), warp_sum(st.cross)};
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 6; ++k)
@@ -723,11 +896,12 @@ cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t
     auto kern = k_transport<R, F>;
     static bool configured = false;   // per instantiation, per process
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes<R, F>(max_block<R, F>()));
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    kern<<<grid, block, kSmemBytes, s>>>(A);
+    kern<<<grid, block, smem_bytes<R, F>(block), s>>>(A);
     return cudaGetLastError();
 }
 
@@ -738,11 +912,12 @@ cudaError_t launch_batch_one(const BatchArgs& B, int grid, int block, cudaStream
     auto kern = k_transport_batch<R, F>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes<R, F>(max_block<R, F>()));
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    kern<<<grid, block, kSmemBytes, s>>>(B);
+    kern<<<grid, block, smem_bytes<R, F>(block), s>>>(B);
     return cudaGetLastError();
 }
 
@@ -751,9 +926,9 @@ int occupancy_one(int block)
 {
     if (block > max_block<R, F>()) return 0;
     auto kern = k_transport<R, F>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<R, F>(max_block<R, F>()));
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, kSmemBytes) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem_bytes<R, F>(block)) != cudaSuccess) return 0;
     return n;
 }
 
