@@ -256,6 +256,7 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.n = n;
     A.k0 = (unsigned)(seed & 0xffffffffu);
     A.k1 = (unsigned)(seed >> 32);
+    A.keys = round_keys(seed);
     A.max_iters = T.max_iters;
     A.refill_min = T.refill_min;
 }
@@ -721,7 +722,7 @@ krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* 
              "upload model arguments");
     KRL_CUDA(cudaMemsetAsync(b->d_counts, 0, n * (1 + ST_N) * sizeof(unsigned long long), s), "reset counters");
     KRL_CUDA(cudaMemsetAsync(b->d_cursor, 0, sizeof(int), s), "reset cursor");
-    BatchArgs B{b->d_args, b->n, b->d_cursor};
+    BatchArgs B{b->d_args, b->n, b->d_cursor, round_keys(seed)};
     KRL_CUDA(launch_transport_batch(B, T.precision, f, grid, T.block, s), "batch launch");
     KRL_CUDA(add_counters_batch(b->d_dst, b->d_counts + n, b->n, s), "accumulate counters");
     if (stats) {

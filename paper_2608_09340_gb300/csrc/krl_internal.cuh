@@ -53,6 +53,27 @@ enum : unsigned {
 
 enum { ST_EMITTED = 0, ST_ESCAPED, ST_DESTROYED, ST_STUCK, ST_SCAT, ST_CROSS, ST_N = 8 };
 
+// Philox4x32-10 round keys of a launch: k[0][r] = key_lo + r 0x9E3779B9,
+// k[1][r] = key_hi + r 0xBB67AE85 (mod 2^32). Precomputed on the host and
+// passed in the kernel's parameter block, so each round reads its keys as
+// constant operands instead of recomputing the schedule per call.
+struct RoundKeys {
+    unsigned k[2][10];
+};
+
+inline RoundKeys round_keys(unsigned long long seed)
+{
+    RoundKeys K;
+    unsigned k0 = (unsigned)(seed & 0xffffffffu), k1 = (unsigned)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k[0][r] = k0;
+        K.k[1][r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+
 struct TransportArgs {
     const float4* cells;      // {line-centre tau per cell width, Vx/b, Vy/b, Vz/b}
     const float* eps;         // per-cell destruction probability or nullptr
@@ -87,6 +108,7 @@ struct TransportArgs {
     krl_packet_record* rec;
     unsigned long long first, n;
     unsigned k0, k1;
+    RoundKeys keys;           // round keys of (k0, k1)
     unsigned long long max_iters;
     int refill_min;
 };
@@ -102,6 +124,7 @@ struct BatchArgs {
     const TransportArgs* models;   // device [n_models]
     int n_models;
     int* cursor;                   // device: lowest model that may still have work
+    RoundKeys keys;                // one seed for every model of the batch
 };
 cudaError_t launch_transport_batch(const BatchArgs& B, int precision, unsigned features, int grid, int block,
                                    cudaStream_t s);

@@ -49,22 +49,19 @@ struct Words {
     uint32_t w[4];
 };
 
-__device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        uint32_t k0, uint32_t k1)
+__device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const RoundKeys& K)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
         uint32_t h0 = __umulhi(m0, c0), l0 = m0 * c0;
         uint32_t h1 = __umulhi(m1, c2), l1 = m1 * c2;
-        uint32_t n0 = h1 ^ c1 ^ k0;
-        uint32_t n2 = h0 ^ c3 ^ k1;
+        uint32_t n0 = h1 ^ c1 ^ K.k[0][r];
+        uint32_t n2 = h0 ^ c3 ^ K.k[1][r];
         c0 = n0;
         c1 = l1;
         c2 = n2;
         c3 = l0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
     }
     return Words{{c0, c1, c2, c3}};
 }
@@ -83,7 +80,6 @@ struct Ops<float> {
         return __uint_as_float((r >> 9) + 0x3f800000u) - 0x1.fffffep-1f;
     }
     static __device__ __forceinline__ float ln(float v) { return __logf(v); }
-    static __device__ __forceinline__ float lg10(float v) { return __log2f(v) * 0.30102999566398120f; }
     static __device__ __forceinline__ float ex(float v) { return __expf(v); }
     // sqrt(v) for v >= 0 as v * rsqrt(v) (one MUFU op, 2 ulp)
     static __device__ __forceinline__ float sq(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
@@ -105,37 +101,53 @@ struct Ops<float> {
         *c = -cc;
     }
     static __device__ __forceinline__ float big() { return 3.0e38f; }
+    // min(1, max(0, p + d n)): one saturating FMA
+    static __device__ __forceinline__ float step01(float p, float d, float n) { return __saturatef(fmaf(d, n, p)); }
+    // position of |x| on the Voigt table, (log10|x| - L0) (N - 1) / (L1 - L0),
+    // as one FMA on log2|x|
+    static __device__ __forceinline__ float vt(float ax)
+    {
+        constexpr double C = (kVoigtN - 1) / (kVoigtL1 - kVoigtL0);
+        return fmaf(__log2f(ax), (float)(C * 0.30102999566398119521), (float)(-kVoigtL0 * C));
+    }
 };
 
 template <>
 struct Ops<double> {
     static __device__ __forceinline__ double uni(uint32_t r) { return (double)(r >> 9) * 0x1p-23 + 0x1p-24; }
     static __device__ __forceinline__ double ln(double v) { return log(v); }
-    static __device__ __forceinline__ double lg10(double v) { return log10(v); }
     static __device__ __forceinline__ double ex(double v) { return exp(v); }
     static __device__ __forceinline__ double sq(double v) { return sqrt(v); }
     static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
     static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
     static __device__ __forceinline__ void sc2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
     static __device__ __forceinline__ double big() { return 1.0e300; }
+    static __device__ __forceinline__ double step01(double p, double d, double n) { return fmin(1.0, fmax(0.0, p + d * n)); }
+    static __device__ __forceinline__ double vt(double ax)
+    {
+        return (log10(ax) - (double)kVoigtL0) * ((kVoigtN - 1) / (kVoigtL1 - kVoigtL0));
+    }
 };
 
 // ---------------------------------------------------------------- table lookups (shared memory)
 
 // H(a, x) from the ph_mode 2 slice: ln H linear in log10|x| between nodes.
+// The three ranges are evaluated without branches and the result selected
+// (every path is finite or discarded for any x).
 template <typename R>
 __device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
 {
     using O = Ops<R>;
-    R ax = fabs(x);
-    if (ax < (R)1e-4) return H0;
-    if (ax > (R)1e3) return a / ((R)1.7724538509055160 * ax * ax) * ((R)1 + (R)1.5 / (ax * ax));
-    R t = (O::lg10(ax) - (R)kVoigtL0) * (R)((kVoigtN - 1) / (kVoigtL1 - kVoigtL0));
+    const R ax = fabs(x);
+    const R t = O::vt(ax);
     int i = (int)t;
     i = i < 0 ? 0 : (i > kVoigtN - 2 ? kVoigtN - 2 : i);
-    R f = t - (R)i;
-    R l0 = (R)sv[i], l1 = (R)sv[i + 1];
-    return O::ex(((R)1 - f) * l0 + f * l1);
+    const R f = t - (R)i;
+    const R l0 = (R)sv[i], l1 = (R)sv[i + 1];
+    const R tab = O::ex(((R)1 - f) * l0 + f * l1);
+    const R ax2 = ax * ax;
+    const R wing = O::dv(a, (R)1.7724538509055160 * ax2) * ((R)1 + O::dv((R)1.5, ax2));
+    return ax < (R)1e-4 ? H0 : (ax > (R)1e3 ? wing : tab);
 }
 
 // Largest row i in [0, 38] with X[i] <= ax: closed-form guess from the node
@@ -144,9 +156,10 @@ __device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
 template <typename R>
 __device__ __forceinline__ int us_row2(R ax, const float* sx, R& x0, R& x1)
 {
-    int i;
-    if (ax < (R)8) i = (int)(ax * (R)2.25);
-    else i = 18 + (int)((R)21 * Ops<R>::ln(ax * (R)0.125) * (R)0.27588297880498553);  // 1/ln(37.5)
+    // both guesses without a branch (the log one is finite for ax >= 0)
+    const int ilin = (int)(ax * (R)2.25);
+    const int ilog = 18 + (int)((R)21 * Ops<R>::ln(ax * (R)0.125) * (R)0.27588297880498553);  // 1/ln(37.5)
+    int i = ax < (R)8 ? ilin : ilog;
     i = i < 0 ? 0 : (i > kUsNx - 2 ? kUsNx - 2 : i);
     x0 = (R)sx[i];
     x1 = (R)sx[i + 1];
@@ -248,9 +261,30 @@ __device__ __forceinline__ void set_dir(Pkt<R>& p, R nx, R ny, R nz)
     p.nx = nx;
     p.ny = ny;
     p.nz = nz;
-    p.ix = Ops<R>::rcp(nx);
-    p.iy = Ops<R>::rcp(ny);
-    p.iz = Ops<R>::rcp(nz);
+    if constexpr (sizeof(R) == 4) {
+        // a zero component counts as +1e-30 (the packet then crosses that
+        // face only from exactly on it), so that 1/n is finite and its sign
+        // alone selects the face ahead
+        p.ix = Ops<R>::rcp(nx != 0.0f ? nx : 1e-30f);
+        p.iy = Ops<R>::rcp(ny != 0.0f ? ny : 1e-30f);
+        p.iz = Ops<R>::rcp(nz != 0.0f ? nz : 1e-30f);
+    } else {
+        p.ix = Ops<R>::rcp(nx);
+        p.iy = Ops<R>::rcp(ny);
+        p.iz = Ops<R>::rcp(nz);
+    }
+}
+
+// Distance (in cell widths) to the face ahead along one axis, from the
+// in-cell coordinate q in [0, 1] and the direction component n with 1/n.
+template <typename R>
+__device__ __forceinline__ R face_dist(R q, R n, R in)
+{
+    if constexpr (sizeof(R) == 4) {
+        return fmaf(-q, in, in > 0.0f ? in : 0.0f);      // (1 - q)/n or -q/n
+    } else {
+        return n > 0.0 ? (1.0 - q) * in : (n < 0.0 ? -q * in : 1.0e300);
+    }
 }
 
 template <typename R>
@@ -297,14 +331,14 @@ __device__ __forceinline__ void write_record(const TransportArgs& A, const Pkt<R
 // Returns false if the source point lies outside the domain (the packet
 // then leaves at once).
 template <typename R, unsigned F>
-__device__ bool emit(const TransportArgs& A, Pkt<R>& p)
+__device__ bool emit(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p)
 {
     using O = Ops<R>;
     const uint32_t lo = (uint32_t)p.id, hi = (uint32_t)(p.id >> 32);
-    Words b0 = philox(lo, hi, 0u, 0u, A.k0, A.k1);
+    Words b0 = philox(lo, hi, 0u, 0u, K);
     const bool need1 = A.src_kind != KRL_SRC_POINT || A.src_profile == KRL_PROFILE_GAUSSIAN;
     Words b1 = {{0u, 0u, 0u, 0u}};
-    if (need1) b1 = philox(lo, hi, 0u, 1u, A.k0, A.k1);
+    if (need1) b1 = philox(lo, hi, 0u, 1u, K);
     const int dims[3] = {A.nx, A.ny, A.nz};
     double X[3];
     R n[3];
@@ -329,7 +363,7 @@ __device__ bool emit(const TransportArgs& A, Pkt<R>& p)
             for (int d = 0; d < 3; ++d)
                 X[d] = (d == A.src_axis) ? A.src_plane : dims[d] * (double)O::uni(b1.w[q++]);
         } else {
-            Words b2 = philox(lo, hi, 0u, 2u, A.k0, A.k1);
+            Words b2 = philox(lo, hi, 0u, 2u, K);
             double uc = (double)(b2.w[0] >> 8) * 0x1p-24 + (double)(b2.w[1] >> 8) * 0x1p-48 + 0x1p-49;
             int l = 0, h = A.ncell - 1;              // first cell with cdf > uc
             while (l < h) {
@@ -403,7 +437,7 @@ template <typename R, unsigned F>
 __device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xcom, R H)
 {
     if ((A.rich & KRL_TALLY_J) && A.n_ch > 0) {
-        R q = (-xcom - (R)A.ch_x0) / (R)A.ch_dx;
+        R q = Ops<R>::dv(-xcom - (R)A.ch_x0, (R)A.ch_dx);
         if (q >= (R)0 && q < (R)A.n_ch) atomicAdd(A.J + (size_t)p.c * A.n_ch + (int)q, (double)ds);
     }
     if (!(A.rich & KRL_TALLY_EMISS) || A.n_ch <= 0) return;
@@ -416,8 +450,8 @@ __device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xc
         g = fmin((R)1, fmax((R)-1, g));
         R vc = (F & F_VEL) ? vdot<R>(cx, cy, cz, p.rec) : (R)0;
         // channels with |x_out,k - x_com| <= 10, x_out,k = -(x0 + (k + 1/2) dx) - vc
-        R ctr = (-(R)A.ch_x0 - vc - xcom) / (R)A.ch_dx - (R)0.5;
-        R span = (R)kRdMax / (R)A.ch_dx;
+        R ctr = Ops<R>::dv(-(R)A.ch_x0 - vc - xcom, (R)A.ch_dx) - (R)0.5;
+        R span = Ops<R>::dv((R)kRdMax, (R)A.ch_dx);
         int k0 = (int)ceil(ctr - span) - 1;
         int k1 = (int)floor(ctr + span) + 1;
         k0 = k0 < 0 ? 0 : k0;
@@ -601,7 +635,8 @@ __device__ __forceinline__ void stash_get(const TransportArgs& A, const uint32_t
 // inside the cell or a crossing of the nearest face). Returns false when the
 // packet has ended (escape, destruction or event budget).
 template <typename R, unsigned F>
-__device__ __forceinline__ bool advance(const TransportArgs& A, Pkt<R>& p, const float* sv, const float* sx,
+__device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p, const float* sv,
+                                        const float* sx,
                                         const float* sc, const unsigned char* sg, R a, R H0, LaneStats& st)
 {
     using O = Ops<R>;
@@ -613,33 +648,35 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, Pkt<R>& p, const
         write_record(A, p, 3);
         return false;
     }
-    // Draw the next scattering's random numbers before the profile lookup
-    // when the last event was a scattering (the common case deep in the
-    // line core): the two Philox chains overlap the lookup's latency.
+    // Draw the next scattering's random numbers up front, for every lane of
+    // the converged group, when any of them last scattered (the common case
+    // deep in the line core): the lanes then share one pass through Philox
+    // instead of the few lanes that follow a face crossing drawing again in
+    // a divergent branch, and the chains overlap the lookup's latency. A
+    // lane whose event turns out to be a crossing discards its draw.
     const uint32_t idlo = (uint32_t)p.id, idhi = (uint32_t)(p.id >> 32);
     Words w0 = {{0u, 0u, 0u, 0u}}, w1 = {{0u, 0u, 0u, 0u}};
-    const bool spec = p.prev_scat;
+    const bool spec = __any_sync(__activemask(), p.prev_scat);
     if (spec) {
-        w0 = philox(idlo, idhi, p.nscat + 1u, 0u, A.k0, A.k1);
-        w1 = philox(idlo, idhi, p.nscat + 1u, 1u, A.k0, A.k1);
+        w0 = philox(idlo, idhi, p.nscat + 1u, 0u, K);
+        w1 = philox(idlo, idhi, p.nscat + 1u, 1u, K);
     }
     const R vdn = (F & F_VEL) ? vdot<R>(p.nx, p.ny, p.nz, p.rec) : (R)0;
     const R xcom = p.x - vdn;
     const R H = voigt<R>(xcom, sv, a, H0);
     const R alpha = (R)p.rec.x * H;
-    const R BIG = O::big();
-    R tx = p.nx > (R)0 ? ((R)1 - p.px) * p.ix : (p.nx < (R)0 ? -p.px * p.ix : BIG);
-    R ty = p.ny > (R)0 ? ((R)1 - p.py) * p.iy : (p.ny < (R)0 ? -p.py * p.iy : BIG);
-    R tz = p.nz > (R)0 ? ((R)1 - p.pz) * p.iz : (p.nz < (R)0 ? -p.pz * p.iz : BIG);
+    const R tx = face_dist<R>(p.px, p.nx, p.ix);
+    const R ty = face_dist<R>(p.py, p.ny, p.iy);
+    const R tz = face_dist<R>(p.pz, p.nz, p.iz);
     R sx_ = tx;
     int axis = 0;
     if (ty < sx_) { sx_ = ty; axis = 1; }
     if (tz < sx_) { sx_ = tz; axis = 2; }
     const bool scat = p.tau < alpha * sx_;
     const R ds = scat ? O::dv(p.tau, alpha) : sx_;
-    p.px = fmin((R)1, fmax((R)0, p.px + ds * p.nx));
-    p.py = fmin((R)1, fmax((R)0, p.py + ds * p.ny));
-    p.pz = fmin((R)1, fmax((R)0, p.pz + ds * p.nz));
+    p.px = O::step01(p.px, ds, p.nx);
+    p.py = O::step01(p.py, ds, p.ny);
+    p.pz = O::step01(p.pz, ds, p.nz);
     if (F & F_RICH) {
         if (A.rich & KRL_TALLY_EXC) p.vis_exc += ds * H;
         if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H);
@@ -651,8 +688,8 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, Pkt<R>& p, const
         ++p.nscat;
         ++p.vis_scat;
         if (!spec) {
-            w0 = philox(idlo, idhi, p.nscat, 0u, A.k0, A.k1);
-            w1 = philox(idlo, idhi, p.nscat, 1u, A.k0, A.k1);
+            w0 = philox(idlo, idhi, p.nscat, 0u, K);
+            w1 = philox(idlo, idhi, p.nscat, 1u, K);
         }
         if ((F & F_RICH) && (A.rich & kRichEps)) {
             if (O::uni(w1.w[2]) < (R)__ldg(A.eps + p.c)) {
@@ -675,7 +712,8 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, Pkt<R>& p, const
         const int gm = us_bin<R>(O::uni(w0.w[0]), L);
         const R tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
         const R z1 = rad * bc, z2 = rad * bs;
-        const R upar = fabs(xcom) > (R)300 ? z2 : us_sample<R>(xcom, L, gm, sx, sc, sg);
+        const R us = us_sample<R>(xcom, L, gm, sx, sc, sg);   // finite for any x; unused beyond 300
+        const R upar = fabs(xcom) > (R)300 ? z2 : us;
         const R g = p.nx * mx + p.ny * my + p.nz * mz;
         const R sg_ = O::sq(fmax((R)0, (R)1 - g * g));
         const R xout = xcom + upar * (g - (R)1) + z1 * sg_;
@@ -692,7 +730,8 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, Pkt<R>& p, const
     const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
     const int stride = axis == 0 ? 1 : (axis == 1 ? A.nx : A.nx * A.ny);
     const int cur = axis == 0 ? p.cx : (axis == 1 ? p.cy : p.cz);
-    const R nd = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+    // side from the sign of 1/n, which selected the face (see set_dir)
+    const R nd = axis == 0 ? p.ix : (axis == 1 ? p.iy : p.iz);
     const int step = nd > (R)0 ? 1 : -1;
     int nc = cur + step;
     int dc = step * stride;
@@ -736,7 +775,7 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, Pkt<R>& p, const
 // then wait at the round barrier without issuing, so the surviving packets
 // run in full warps instead of sharing the issue slots with idle lanes.
 template <typename R, unsigned F>
-__device__ __forceinline__ void run_model(const TransportArgs& A, float* sm)
+__device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKeys& K, float* sm)
 {
     int* ctl = reinterpret_cast<int*>(reinterpret_cast<char*>(sm) + kCtlOff);
     uint32_t* stash = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + kStashOff);
@@ -784,7 +823,7 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, float* sm)
                     if (k < A.n) {
                         p.id = A.first + k;
                         ++st.emit;
-                        if (emit<R, F>(A, p)) {
+                        if (emit<R, F>(A, K, p)) {
                             active = true;
                         } else {
                             spectrum_add(A, (double)p.x);
@@ -827,7 +866,7 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, float* sm)
             it = 0;
         }
         if (!bulk) ++it;
-        if (active) active = advance<R, F>(A, p, sv, sx, sc, sg, a, H0, st);
+        if (active) active = advance<R, F>(A, K, p, sv, sx, sc, sg, a, H0, st);
     }
 
     const unsigned long long tot[6] = {warp_sum(st.emit), warp_sum(st.esc),  warp_sum(st.des),
@@ -843,7 +882,7 @@ template <typename R, unsigned F>
 __global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport(const __grid_constant__ TransportArgs A)
 {
     extern __shared__ float sm[];
-    run_model<R, F>(A, sm);
+    run_model<R, F>(A, A.keys, sm);
 }
 
 // The lowest-numbered model that still has unassigned packet ids, or -1.
@@ -884,7 +923,7 @@ __global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport_batch(const 
             for (int i = threadIdx.x; i < (int)(sizeof(TransportArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
-        run_model<R, F>(sA, sm);
+        run_model<R, F>(sA, B.keys, sm);
         __syncthreads();     // every warp done before the tables are replaced
     }
 }
