@@ -2,13 +2,14 @@
 uniform sphere (T = 1e4 K, a = 4.7e-4, central point source at line centre,
 FP32 walk, 400-bin escaped spectrum and per-cell scattering map).
 
-One step = one krl_run_packets launch over the next PACKETS_PER_STEP packet
-ids of the 1e6-packet job (every step of the pass runs: emission, cell walk,
-scattering, tallies, escape, regeneration, counter reduction). Inputs are
-resident on the device; L2 is flushed (a 256 MiB write) before every timed
-step. Steps rotate over --streams streams (default 2) so that one step's
-tail overlaps the next step's start (--serial: one stream); the K steps are bracketed by
-CUDA events, and every launch also by its own pair on its stream.
+One step = one krl_run_packets launch over a whole 1e6-packet job (the next
+1e6 packet ids; every part of the pass runs: emission, cell walk, scattering,
+tallies, escape, regeneration, counter reduction). Inputs are resident on
+the device; L2 is flushed (a 256 MiB write) before every timed step. Steps
+rotate over --streams streams (default 2) so that one job's tail (its last,
+longest packets) overlaps the next job's start (--serial: one stream); the
+K steps are bracketed by CUDA events, and every launch also by its own pair
+on its stream.
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload instead.
@@ -27,8 +28,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PACKETS_PER_STEP = 1 << 19
 JOB_PACKETS = 1_000_000
+PACKETS_PER_STEP = JOB_PACKETS
+E2E_MAX_STEPS = 3
 METRIC = "scatterings/s & packets/s (64³ τ0=1e6 sphere)"
 UNIT = "scatterings/s"
 # Algorithmic lane operations per event (derivation in the design doc): a
@@ -288,7 +290,7 @@ def cpu_baseline(p):
     """Oracle on a bounded sample (about 10 s of host work) at N = 1, rank 0."""
     import oracle
     cores = os.cpu_count() or 1
-    n = 4 * cores
+    n = 24 * cores                  # about 10 s at the oracle's ~40 packets/s on 16 cores
     oracle.line_tables(float(p.line.a_fixed), False)
     t0 = time.perf_counter()
     r = oracle.run(p, n=n, first=JOB_PACKETS - n, nthreads=cores)
@@ -403,7 +405,8 @@ def main():
         barrier()
         t0 = time.perf_counter()
         e_scat = 0
-        for k in range(args.steps):
+        e2e_steps = min(args.steps, E2E_MAX_STEPS)
+        for k in range(e2e_steps):
             q = W.sphere(vmax_kms=0.0, tau0=args.tau0)
             q.opacity = op_host          # host buffer: copied by the binding's marshalling
             gg = krl.Grid(q, device=dev)
@@ -420,7 +423,8 @@ def main():
         shard.sum_over_ranks(et)
         e2e = {"value": float(et.item()) / e_dt, "unit": UNIT,
                "h2d_bytes_per_step": int(op_host.numel() * 4),
-               "d2h_bytes_per_step": int(spec_h.numel() * 8 + scat_h.numel() * 8)}
+               "d2h_bytes_per_step": int(spec_h.numel() * 8 + scat_h.numel() * 8), "steps": e2e_steps,
+               "path": "Grid from pinned host fields: grid creation, line tables, run, tally reads"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
