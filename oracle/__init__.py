@@ -61,6 +61,7 @@ class _Problem(C.Structure):
         ("n_ch", C.c_int), ("ch_x0", C.c_double), ("ch_dx", C.c_double),
         ("n_cam", C.c_int), ("cam_dir", C.POINTER(C.c_double)),
         ("tally_flags", C.c_uint), ("max_iters", C.c_uint64),
+        ("ph_mode", C.c_int), ("voigt2d", C.POINTER(C.c_double)), ("u0", C.c_double),
     ]
 
 
@@ -96,6 +97,12 @@ def _lib():
     lib.orc_rkernel.restype = C.c_double
     lib.orc_rkernel.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, C.c_double]
     return lib
+
+
+@functools.lru_cache(maxsize=1)
+def voigt2d_f64():
+    """The ph_mode 1 table (float32 values) as a contiguous FP64 array."""
+    return np.ascontiguousarray(T.voigt2d_table(), dtype=np.float64)
 
 
 def _dp(a):
@@ -193,6 +200,15 @@ def run(problem, n: int | None = None, first: int = 0, seed: int | None = None,
     P.cam_dir = _dp(d["cam"])
     P.tally_flags = flags
     P.max_iters = max_iters
+    ph = int(getattr(problem.line, "ph_mode", 2) or 2)
+    P.ph_mode = ph
+    if ph == 1:
+        T.voigt2d_weights(float(d["a"]))          # range check
+        v2 = voigt2d_f64()
+        keep.append(v2)
+        P.voigt2d = _dp(v2)
+    elif ph == 3:
+        P.u0 = T.blend_u0(float(d["a"]))
     ncam = max(1, len(problem.cameras))
     out = {
         "spec_w": np.zeros(problem.spectrum[2] + 2), "spec_c": np.zeros(problem.spectrum[2] + 2, np.uint64),
@@ -232,14 +248,21 @@ def _problem_for_lookups(a: float, tb: dict):
     return P
 
 
-def c_lookups(a: float):
+def c_lookups(a: float, ph_mode: int = 2):
     """The C walk's own sampler, profile and kernel lookups, for the tests."""
     tb = line_tables(a, True)
     P = _problem_for_lookups(a, tb)
+    P.ph_mode = ph_mode
+    v2 = None
+    if ph_mode == 1:
+        v2 = voigt2d_f64()
+        P.voigt2d = _dp(v2)
+    elif ph_mode == 3:
+        P.u0 = T.blend_u0(a)
     lib = _lib()
 
     class L:
-        keep = (tb, P)
+        keep = (tb, P, v2)
 
         @staticmethod
         def us_sample(x, xi):

@@ -18,6 +18,8 @@ Contents and the passages they follow:
 * ``voigt_table`` / ``voigt_lookup``       - the 1-D log-frequency Voigt table
   of ph_mode 2 (Sec. 2.2.1, 2.3.1). Grid and interpolation are a reading
   (the paper gives only "5000 points in logarithmic frequency").
+* ``voigt2d_*`` / ``blend_*``              - the ph_mode 1 two-dimensional
+  Voigt table and the ph_mode 3 core-wing blend (Sec. 2.3.1).
 * ``usampler_*``                           - the velocity sampler p(u_par | x_in)
   (Sec. 2.1.1): 40 x-nodes, 251 u-nodes on [-6, 6], log of the normalised
   cumulative distribution.
@@ -108,6 +110,103 @@ def voigt_lookup(x, a: float, lnH, H0):
     L = np.asarray(lnH, dtype=np.float64)
     out[mid] = np.exp((1.0 - f) * L[i] + f * L[i + 1])
     return out
+
+
+# ---------------------------------------------------------------- ph_mode 1 and 3 profiles
+#
+# Sec. 2.3.1 describes three photon modes. ph_mode 2 is the slice above.
+# ph_mode 1 keeps a two-dimensional Voigt table (64 logarithmically spaced
+# damping parameters by 512 frequency points) in global memory; its grid
+# and interpolation are readings (the paper gives only the counts): a nodes
+# uniform in log10 a over [-6, 0], x nodes uniform in log10|x| over [-4, 3],
+# the table holds ln H, looked up bilinearly in (log10 a, log10|x|).
+# ph_mode 3 replaces the tabulated profile by a blend of the Doppler core
+# exp(-x^2) and the damping wing a / (sqrt(pi) (x^2 + a^2)) with the switch
+# w = [1 + tanh(2|x| - 2 u0)] / 2 at the crossing point u0 of the two.
+
+V2_NA = 64
+V2_NX = 512
+V2_LA_MIN = -6.0
+V2_LA_MAX = 0.0
+
+
+def voigt2d_anodes():
+    return 10.0 ** (V2_LA_MIN + (V2_LA_MAX - V2_LA_MIN) * np.arange(V2_NA) / (V2_NA - 1))
+
+
+def voigt2d_xnodes():
+    return 10.0 ** (VOIGT_LOG10_MIN + (VOIGT_LOG10_MAX - VOIGT_LOG10_MIN) * np.arange(V2_NX) / (V2_NX - 1))
+
+
+def voigt2d_table():
+    """ln H(a_j, x_i) at the ph_mode 1 nodes, [64, 512], stored as float32."""
+    A = voigt2d_anodes()
+    X = voigt2d_xnodes()
+    tab = np.empty((V2_NA, V2_NX))
+    for j, a in enumerate(A):
+        tab[j] = np.log(voigt_H(a, X))
+    return tab.astype(np.float32)
+
+
+def voigt2d_weights(a: float):
+    """Row j and weight w of damping parameter a on the table's a axis:
+    log10 a = (1 - w) log10 a_j + w log10 a_{j+1}. a must lie in [1e-6, 1]."""
+    if not (10.0 ** V2_LA_MIN <= a <= 10.0 ** V2_LA_MAX):
+        raise ValueError(f"a = {a} outside the ph_mode 1 table [1e-6, 1]")
+    s = (math.log10(a) - V2_LA_MIN) * ((V2_NA - 1) / (V2_LA_MAX - V2_LA_MIN))
+    j = min(max(int(math.floor(s)), 0), V2_NA - 2)
+    return j, s - j
+
+
+def voigt2d_lookup(x, a: float, tab):
+    """ph_mode 1 lookup of H(a, x): bilinear in (log10 a, log10|x|) of ln H;
+    |x| below the first node uses the first node; the wing series
+    a / (sqrt(pi) x^2) (1 + 3/(2 x^2)) above |x| = 1e3."""
+    j, w = voigt2d_weights(a)
+    ax = np.abs(np.asarray(x, dtype=np.float64))
+    out = np.empty_like(ax)
+    hi = ax > 1e3
+    xh = ax[hi]
+    out[hi] = a / (SQRT_PI * xh * xh) * (1.0 + 1.5 / (xh * xh))
+    m = ~hi
+    t = (np.log10(np.maximum(ax[m], 10.0 ** VOIGT_LOG10_MIN)) - VOIGT_LOG10_MIN) * \
+        ((V2_NX - 1) / (VOIGT_LOG10_MAX - VOIGT_LOG10_MIN))
+    t = np.maximum(t, 0.0)
+    i = np.clip(np.floor(t).astype(np.int64), 0, V2_NX - 2)
+    f = t - i
+    T0 = np.asarray(tab[j], dtype=np.float64)
+    T1 = np.asarray(tab[j + 1], dtype=np.float64)
+    lo_row = (1.0 - f) * T0[i] + f * T0[i + 1]
+    hi_row = (1.0 - f) * T1[i] + f * T1[i + 1]
+    out[m] = np.exp((1.0 - w) * lo_row + w * hi_row)
+    return out
+
+
+def blend_u0(a: float) -> float:
+    """Crossing point u0 > 0 of the core exp(-u^2) and the wing
+    a / (sqrt(pi) (u^2 + a^2)) that separates core from wing: the larger
+    root of g(u) = -u^2 - ln(a / (sqrt(pi) (u^2 + a^2))). g is largest at
+    u* = sqrt(1 - a^2) and falls without bound beyond it, so the root is
+    bracketed by [u*, 30] when g(u*) > 0 (a below about 0.8)."""
+    from scipy.optimize import brentq
+
+    def g(u):
+        return -u * u - math.log(a / (SQRT_PI * (u * u + a * a)))
+
+    if not (0.0 < a < 1.0):
+        raise ValueError("ph_mode 3 needs 0 < a < 1")
+    us = math.sqrt(1.0 - a * a)
+    if g(us) <= 0.0:
+        raise ValueError(f"core and wing do not cross for a = {a}")
+    return brentq(g, us, 30.0, xtol=1e-15, rtol=1e-15, maxiter=200)
+
+
+def blend_H(x, a: float, u0: float):
+    """ph_mode 3 profile: (1 - w) exp(-x^2) + w a / (sqrt(pi) (x^2 + a^2)),
+    w = [1 + tanh(2|x| - 2 u0)] / 2."""
+    ax = np.abs(np.asarray(x, dtype=np.float64))
+    w = 0.5 * (1.0 + np.tanh(2.0 * ax - 2.0 * u0))
+    return (1.0 - w) * np.exp(-ax * ax) + w * a / (SQRT_PI * (ax * ax + a * a))
 
 
 # ---------------------------------------------------------------- USampler

@@ -93,6 +93,9 @@ typedef struct {
     const double* cam_dir;   /* [n_cam][3] unit propagation directions toward cameras */
     unsigned tally_flags;
     uint64_t max_iters;      /* per-packet cap on walk iterations */
+    int ph_mode;             /* 2: the 1-D slice; 1: the 2-D table; 3: core-wing blend */
+    const double* voigt2d;   /* [64][512] ln H for ph_mode 1 */
+    double u0;               /* core-wing crossing point for ph_mode 3 */
 } orc_problem;
 
 typedef struct {
@@ -156,9 +159,49 @@ void orc_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, in
 
 /* ------------------------------------------------------------ profile, sampler, kernel */
 
+/* ph_mode 1 (Sec. 2.3.1): bilinear lookup of ln H in (log10 a, log10|x|)
+ * on the two-dimensional table; a nodes uniform in log10 a over [-6, 0]
+ * (64), x nodes uniform in log10|x| over [-4, 3] (512). */
+#define V2_NA 64
+#define V2_NX 512
+#define V2_LA_MIN (-6.0)
+#define V2_LA_MAX 0.0
+
+static double voigt2d_lookup(const orc_problem* P, double ax)
+{
+    if (ax > 1e3) return P->a / (sqrt(ORC_PI) * ax * ax) * (1.0 + 1.5 / (ax * ax));
+    double s = (log10(P->a) - V2_LA_MIN) * ((V2_NA - 1) / (V2_LA_MAX - V2_LA_MIN));
+    int j = (int)floor(s);
+    if (j < 0) j = 0;
+    if (j > V2_NA - 2) j = V2_NA - 2;
+    double w = s - j;
+    double t = (log10(ax < 1e-4 ? 1e-4 : ax) - V_LMIN) * ((V2_NX - 1) / (V_LMAX - V_LMIN));
+    if (t < 0.0) t = 0.0;
+    int i = (int)floor(t);
+    if (i > V2_NX - 2) i = V2_NX - 2;
+    double f = t - i;
+    const double* r0 = P->voigt2d + (size_t)j * V2_NX;
+    const double* r1 = r0 + V2_NX;
+    double l0 = (1.0 - f) * r0[i] + f * r0[i + 1];
+    double l1 = (1.0 - f) * r1[i] + f * r1[i + 1];
+    return exp((1.0 - w) * l0 + w * l1);
+}
+
+/* ph_mode 3 (Sec. 2.3.1): (1 - w) exp(-x^2) + w a / (sqrt(pi) (x^2 + a^2))
+ * with w = [1 + tanh(2|x| - 2 u0)] / 2 = 1 / (1 + exp(4 (u0 - |x|))). */
+static double blend_lookup(const orc_problem* P, double ax)
+{
+    double w = 1.0 / (1.0 + exp(4.0 * (P->u0 - ax)));
+    double core = exp(-ax * ax);
+    double wing = P->a / (sqrt(ORC_PI) * (ax * ax + P->a * P->a));
+    return (1.0 - w) * core + w * wing;
+}
+
 static double voigt_lookup(const orc_problem* P, double x)
 {
     double ax = fabs(x);
+    if (P->ph_mode == 1) return voigt2d_lookup(P, ax);
+    if (P->ph_mode == 3) return blend_lookup(P, ax);
     if (ax < 1e-4) return P->voigt_H0;
     if (ax > 1e3) return P->a / (sqrt(ORC_PI) * ax * ax) * (1.0 + 1.5 / (ax * ax));
     double t = (log10(ax) - V_LMIN) * ((V_N - 1) / (V_LMAX - V_LMIN));

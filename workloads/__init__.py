@@ -56,6 +56,7 @@ class Line:
     g_l: float = 1.0
     k_ul: float = 0.0          # collisional de-excitation coefficient [cm^3 s^-1]
     a_fixed: float = 0.0       # > 0: damping parameter given directly
+    ph_mode: int = 2           # profile mode: 2 = 1-D slice, 1 = 2-D table, 3 = core-wing blend
 
 
 @dataclasses.dataclass
