@@ -137,6 +137,18 @@ typedef struct {
     int n_cam;
     double cam_theta[KRL_MAX_CAMERAS], cam_phi[KRL_MAX_CAMERAS];
     uint32_t tally_flags;       /* KRL_TALLY_*                                      */
+    /* line-profile mode (Sec. 2.3.1); the velocity sampler is the same in all:
+       0 or 2: the Voigt slice at this a, tables in shared memory (production);
+       1: H(a, x) from a two-dimensional table of ln H over 64 damping parameters
+          (log10 a uniform on [-6, 0]) by 512 frequencies (log10|x| uniform on
+          [-4, 3]) in global memory, bilinear in (log10 a, log10|x|), and the
+          sampler read from global memory; needs 1e-6 <= a <= 1;
+       3: the core-wing approximation (1 - w) exp(-x^2) + w a / (sqrt(pi)(x^2 +
+          a^2)), w = [1 + tanh(2|x| - 2 u0)] / 2, u0 the outer crossing point of
+          the two terms; a demonstration, not for production; needs a < 0.8.
+       Modes 1 and 3 run krl_run_packets only (KRL_ERR_ARG from krl_batch_run
+       and krl_raytrace_channels, which use the mode 2 slice).                 */
+    int ph_mode;
 } krl_line_desc;
 
 /*
@@ -227,7 +239,8 @@ typedef enum {
     KRL_OUT_CELLS = 20,   /* float4 [ncell]: {alpha0 dx, Vx/b, Vy/b, Vz/b}         */
     KRL_OUT_EPS = 21,     /* [ncell]: destruction probability (when k_ul, n_coll)  */
     KRL_OUT_SRC_CDF = 22, /* double [ncell]: emission CDF (volume source)         */
-    KRL_OUT_H0 = 23       /* [1]: H(a, 0)                                          */
+    KRL_OUT_H0 = 23,      /* [1]: H(a, 0)                                          */
+    KRL_OUT_VOIGT2D = 24  /* [64][512]: ln H of ph_mode 1 (built on its first use)  */
 } krl_tally_kind;
 
 /*

@@ -31,10 +31,11 @@ KRL_TALLY = {"scatmap": 1, "exc": 2, "J": 4, "emiss": 8}
 KRL_PREC_FP32, KRL_PREC_FP64 = 0, 1
 KRL_MAX_CAMERAS = 8
 OUT = {"spec_w": 0, "spec_n": 1, "scatmap": 2, "exc": 3, "J": 4, "emiss": 5, "stats": 6,
-       "voigt": 16, "us_x": 17, "us_lncdf": 18, "rtab": 19, "cells": 20, "eps": 21, "src_cdf": 22, "H0": 23}
+       "voigt": 16, "us_x": 17, "us_lncdf": 18, "rtab": 19, "cells": 20, "eps": 21, "src_cdf": 22, "H0": 23,
+       "voigt2d": 24}
 OUT_DTYPE = {0: "float64", 1: "int64", 2: "int64", 3: "float64", 4: "float64", 5: "float32", 6: "int64",
              16: "float32", 17: "float32", 18: "float32", 19: "float32", 20: "float32", 21: "float32",
-             22: "float64", 23: "float32"}
+             22: "float64", 23: "float32", 24: "float32"}
 
 
 class KrlError(RuntimeError):
@@ -59,7 +60,8 @@ class krl_line_desc(C.Structure):
                 ("luminosity", C.c_double), ("spec_xmin", C.c_double), ("spec_xmax", C.c_double),
                 ("spec_nbins", C.c_int), ("ch_vmin_cms", C.c_double), ("ch_dv_cms", C.c_double),
                 ("n_ch", C.c_int), ("n_cam", C.c_int), ("cam_theta", C.c_double * KRL_MAX_CAMERAS),
-                ("cam_phi", C.c_double * KRL_MAX_CAMERAS), ("tally_flags", C.c_uint32)]
+                ("cam_phi", C.c_double * KRL_MAX_CAMERAS), ("tally_flags", C.c_uint32),
+                ("ph_mode", C.c_int)]
 
 
 class krl_line_info(C.Structure):
@@ -280,6 +282,7 @@ class Grid:
             L = krl_line_desc()
             L.nu0_hz, L.mass_amu, L.A_ul = ln.nu0_hz, ln.mass_amu, ln.A_ul
             L.g_u, L.g_l, L.k_ul, L.a_fixed = ln.g_u, ln.g_l, ln.k_ul, ln.a_fixed
+            L.ph_mode = int(getattr(ln, "ph_mode", 2))
             L.src_kind = KRL_SRC[src.kind]
             L.src_pos = (C.c_double * 3)(*src.pos)
             L.src_axis, L.src_plane = src.axis, src.plane

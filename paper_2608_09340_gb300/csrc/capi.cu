@@ -59,6 +59,11 @@ struct krl_grid {
     float* lv_rate = nullptr;            // [ncell] source rate of the current line
     double* lv_total = nullptr;          // [1]
     unsigned long long* lv_change = nullptr;
+    // line-profile modes 1 and 3 (krl_line_desc.ph_mode)
+    float* voigt2d = nullptr;            // [kV2Na][kV2Nx], built once on first use
+    int v2_row = 0;
+    double v2_w = 0.0;
+    double u0 = 0.0;
 };
 
 namespace {
@@ -152,6 +157,7 @@ size_t tally_elems(const krl_grid* g, krl_tally_kind k, size_t* esz)
     case KRL_OUT_EPS: *esz = 4; return g->eps ? (size_t)g->ncell : 0;
     case KRL_OUT_SRC_CDF: *esz = 8; return g->src_cdf ? (size_t)g->ncell : 0;
     case KRL_OUT_H0: *esz = 4; return g->tab.H0 ? 1 : 0;
+    case KRL_OUT_VOIGT2D: *esz = 4; return g->voigt2d ? (size_t)kV2Na * kV2Nx : 0;
     }
     *esz = 0;
     return 0;
@@ -175,6 +181,7 @@ const void* tally_ptr(const krl_grid* g, krl_tally_kind k)
     case KRL_OUT_EPS: return g->eps;
     case KRL_OUT_SRC_CDF: return g->src_cdf;
     case KRL_OUT_H0: return g->tab.H0;
+    case KRL_OUT_VOIGT2D: return g->voigt2d;
     }
     return nullptr;
 }
@@ -215,7 +222,7 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.nz = g->nz;
     A.ncell = g->ncell;
     A.periodic = g->periodic;
-    A.a = (float)g->info.a;
+    A.a = g->info.a;
     A.H0 = g->tab.H0;
     A.voigt_lnH = g->tab.voigt_lnH;
     A.us_x = g->tab.us_x;
@@ -259,6 +266,31 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.keys = round_keys(seed);
     A.max_iters = T.max_iters;
     A.refill_min = T.refill_min;
+    A.ph_mode = g->line.ph_mode;
+    A.voigt2d = g->voigt2d;
+    A.v2_row = g->v2_row;
+    A.v2_w = g->v2_w;
+    A.u0 = g->u0;
+}
+
+// Crossing point u0 of the ph_mode 3 blend: the outer root of
+// g(u) = -u^2 - ln(a / (sqrt(pi) (u^2 + a^2))) (core = wing), bracketed by
+// [sqrt(1 - a^2), 30], where g has its maximum and is negative; found by
+// bisection to the last bit. False when core and wing do not cross.
+bool blend_crossing(double a, double* u0)
+{
+    if (!(a > 0.0 && a < 1.0)) return false;
+    auto gf = [a](double u) { return -u * u - log(a / (sqrt(kPiD) * (u * u + a * a))); };
+    double lo = sqrt(1.0 - a * a), hi = 30.0;
+    if (!(gf(lo) > 0.0)) return false;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (gf(mid) > 0.0) lo = mid;
+        else hi = mid;
+    }
+    *u0 = 0.5 * (lo + hi);
+    return true;
 }
 
 krl_status resolve_tune(const krl_tune* tune, krl_tune& T)
@@ -370,6 +402,7 @@ krl_status krl_grid_destroy(krl_grid* g)
     dfree(g->lv_rate);
     dfree(g->lv_total);
     dfree(g->lv_change);
+    dfree(g->voigt2d);
     dfree(g->stats);
     dfree(g->run_stats);
     dfree(g->next);
@@ -398,6 +431,7 @@ krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
         if (!isfinite(d->src_pos[k])) return fail(KRL_ERR_ARG, "src_pos must be finite");
     if (d->spec_nbins < 1 || !(d->spec_xmax > d->spec_xmin)) return fail(KRL_ERR_ARG, "bad spectrum binning");
     if (d->tally_flags & ~15u) return fail(KRL_ERR_ARG, "unknown tally flag bits");
+    if (d->ph_mode < 0 || d->ph_mode > 3) return fail(KRL_ERR_ARG, "ph_mode must be 0..3");
     bool need_ch = d->tally_flags & (KRL_TALLY_J | KRL_TALLY_EMISS);
     if (need_ch && (d->n_ch < 1 || !(d->ch_dv_cms > 0))) return fail(KRL_ERR_ARG, "channels need n_ch >= 1, dv > 0");
     if ((d->tally_flags & KRL_TALLY_EMISS) && (d->n_cam < 1 || d->n_cam > KRL_MAX_CAMERAS))
@@ -409,6 +443,7 @@ krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
     // keep a channel grid for the ray trace even without J / emissivity tallies
     if (!need_ch && !(d->n_ch >= 1 && d->ch_dv_cms > 0)) L.n_ch = 0;
     if (!(L.tally_flags & KRL_TALLY_EMISS)) L.n_cam = 0;
+    if (L.ph_mode == 0) L.ph_mode = 2;
     g->line = L;
 
     // scalar line constants (Sec. 2.1, Eq. xdef, Eq. sigma0)
@@ -419,6 +454,22 @@ krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
     I.sigma0_cm2 = (L.g_u / L.g_l) * L.A_ul * kC * kC * kC / (8.0 * pow(kPiD, 1.5) * pow(L.nu0_hz, 3) * I.b_cms);
     I.ncell = g->ncell;
     g->info = I;
+    if (L.ph_mode == 1) {
+        if (!(I.a >= pow(10.0, kV2LaMin) && I.a <= pow(10.0, kV2LaMax))) {
+            free_line(g);
+            return fail(KRL_ERR_ARG, "ph_mode 1 needs 1e-6 <= a <= 1 (a = %g)", I.a);
+        }
+        const double s2 = (log10(I.a) - kV2LaMin) * ((kV2Na - 1) / (kV2LaMax - kV2LaMin));
+        int j = (int)floor(s2);
+        j = j < 0 ? 0 : (j > kV2Na - 2 ? kV2Na - 2 : j);
+        g->v2_row = j;
+        g->v2_w = s2 - j;
+    } else if (L.ph_mode == 3) {
+        if (!blend_crossing(I.a, &g->u0)) {
+            free_line(g);
+            return fail(KRL_ERR_ARG, "ph_mode 3: core and wing do not cross at a = %g", I.a);
+        }
+    }
 
     const size_t n = (size_t)g->ncell;
     const bool with_r = (L.tally_flags & KRL_TALLY_EMISS) != 0;
@@ -468,6 +519,10 @@ krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
     F.eps = g->eps;
     e = derive_fields(F, s);
     if (e == cudaSuccess) e = build_line_tables(I.a, g->tab, with_r, s);
+    if (e == cudaSuccess && L.ph_mode == 1 && !g->voigt2d) {
+        e = dalloc(&g->voigt2d, (size_t)kV2Na * kV2Nx);
+        if (e == cudaSuccess) e = build_voigt2d(g->voigt2d, g->tab.work, s);
+    }
     if (e == cudaSuccess && L.src_kind == KRL_SRC_VOLUME)
         e = emission_cdf(g->src_rate, g->ncell, g->src_cdf, g->scan_work, g->scan_work_n, g->bad, s);
     if (e != cudaSuccess) {
@@ -521,7 +576,7 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     const int maxb = transport_max_block(T.precision, f);
     if (!tune || !tune->block) T.block = maxb;
     else if (T.block > maxb) return fail(KRL_ERR_ARG, "block %d exceeds %d for this walk", T.block, maxb);
-    int occ = transport_occupancy(T.precision, f, T.block);
+    int occ = transport_occupancy(T.precision, f, T.block, g->line.ph_mode);
     if (occ < 1) return fail(KRL_ERR_CUDA, "transport kernel cannot be resident at block %d", T.block);
     int per_sm = T.ctas_per_sm > 0 ? (T.ctas_per_sm < occ ? T.ctas_per_sm : occ) : occ;
     int grid = g->num_sms * per_sm;
@@ -557,6 +612,7 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
 {
     if (!g || !d || !maps) return fail(KRL_ERR_ARG, "krl_raytrace_channels: NULL argument");
     if (!g->line_ok) return fail(KRL_ERR_STATE, "krl_raytrace_channels before krl_line_set");
+    if (g->line.ph_mode != 2) return fail(KRL_ERR_ARG, "the ray trace uses the ph_mode 2 profile slice");
     const krl_line_desc& L = g->line;
     if (L.n_ch < 1 || L.n_ch > 128) return fail(KRL_ERR_ARG, "ray trace needs 1..128 line channels (line has %d)", L.n_ch);
     if (d->npix_x < 1 || d->npix_y < 1 || !(d->fov_cells > 0) || !isfinite(d->fov_cells))
@@ -652,6 +708,7 @@ krl_status krl_batch_create(krl_batch** out, krl_grid* const* grids, int n_model
     for (int m = 0; m < n_models; ++m) {
         if (!grids[m]) return fail(KRL_ERR_ARG, "grid %d is NULL", m);
         if (!grids[m]->line_ok) return fail(KRL_ERR_STATE, "grid %d has no line", m);
+        if (grids[m]->line.ph_mode != 2) return fail(KRL_ERR_ARG, "grid %d: the batched launch runs ph_mode 2 only", m);
         if (grids[m]->device != dev) return fail(KRL_ERR_ARG, "grid %d lives on another device", m);
     }
     krl_batch* b = new (std::nothrow) krl_batch();

@@ -79,7 +79,7 @@ struct TransportArgs {
     const float* eps;         // per-cell destruction probability or nullptr
     int nx, ny, nz, ncell;
     unsigned periodic;        // bit d set: axis d periodic
-    float a;
+    double a;                 // damping parameter (the FP32 walk rounds it once)
     const float* H0;          // device scalar H(a, 0)
     const float* voigt_lnH;
     const float* us_x;
@@ -111,9 +111,25 @@ struct TransportArgs {
     RoundKeys keys;           // round keys of (k0, k1)
     unsigned long long max_iters;
     int refill_min;
+    // line-profile mode (krl_line_desc.ph_mode: 2, or 1 / 3 below)
+    int ph_mode;
+    const float* voigt2d;     // [kV2Na][kV2Nx] ln H, mode 1
+    int v2_row;               // mode 1: rows v2_row, v2_row + 1 bracket log10 a
+    double v2_w;              // mode 1: weight of row v2_row + 1
+    double u0;                // mode 3: core-wing crossing point
 };
 
 constexpr unsigned kRichEps = 1u << 16;
+
+// Two-dimensional Voigt table of line-profile mode 1: ln H(a_j, x_i), a_j
+// uniform in log10 a on [kV2LaMin, kV2LaMax], x_i uniform in log10|x| on
+// [kVoigtL0, kVoigtL1].
+constexpr int kV2Na = 64;
+constexpr int kV2Nx = 512;
+constexpr double kV2LaMin = -6.0;
+constexpr double kV2LaMax = 0.0;
+// work: at least 64 doubles of device scratch.
+cudaError_t build_voigt2d(float* out, double* work, cudaStream_t s);
 
 // Launch the walk (transport.cu). grid/block chosen by the caller.
 cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned features,
@@ -130,7 +146,11 @@ cudaError_t launch_transport_batch(const BatchArgs& B, int precision, unsigned f
                                    cudaStream_t s);
 
 // Occupancy of one instantiation (CTAs per SM at this block size).
-int transport_occupancy(int precision, unsigned features, int block);
+int transport_occupancy(int precision, unsigned features, int block, int ph_mode = 2);
+// Line-profile modes 1 and 3 (transport_modes.cu).
+cudaError_t launch_transport_ph(const TransportArgs& A, int ph_mode, int precision, unsigned features, int grid,
+                                int block, cudaStream_t s);
+int transport_occupancy_ph(int ph_mode, int precision, unsigned features, int block);
 // Largest CTA the instantiation is compiled for (512 lean FP32, else 256).
 int transport_max_block(int precision, unsigned features);
 

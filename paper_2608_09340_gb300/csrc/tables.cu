@@ -48,6 +48,19 @@ __global__ void k_voigt(double a, const double* c, int N, double L, float* lnH, 
     if (i == 0) *H0 = (float)voigt_H(a, 0.0, c, N, L);
 }
 
+// Line-profile mode 1 table: ln H(a_j, x_i) with log10 a_j uniform on
+// [kV2LaMin, kV2LaMax] (kV2Na nodes) and log10 x_i uniform on [kVoigtL0,
+// kVoigtL1] (kV2Nx nodes); one thread per entry.
+__global__ void k_voigt2d(const double* c, int N, double L, float* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kV2Na * kV2Nx) return;
+    const int j = k / kV2Nx, i = k % kV2Nx;
+    const double a = pow(10.0, kV2LaMin + (kV2LaMax - kV2LaMin) * j / (kV2Na - 1));
+    const double x = pow(10.0, kVoigtL0 + (kVoigtL1 - kVoigtL0) * i / (kV2Nx - 1));
+    out[k] = (float)log(voigt_H(a, x, c, N, L));
+}
+
 // Mass of p(u | x) in the u-cell [lo, hi]: the Lorentz factor L(u) times
 // the second-order expansion of exp(-u^2) about the midpoint m, integrated
 // exactly: exp(-m^2) [I0 - 2 m I1 + (2 m^2 - 1) I2], Ik = int (u-m)^k L du.
@@ -294,6 +307,15 @@ cudaError_t build_line_tables(double a, const LineTables& T, bool with_r, cudaSt
         k_rmasses<<<(kRnX + 127) / 128, 128, 0, s>>>(a, p);
         k_rtable<<<(unsigned)((kRtabElems + 255) / 256), 256, 0, s>>>(p, T.rtab);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t build_voigt2d(float* out, double* work, cudaStream_t s)
+{
+    const int N = kWeidemanN;
+    const double L = weideman_L(N);
+    k_weideman<<<1, 64, 0, s>>>(work, N, L);
+    k_voigt2d<<<(kV2Na * kV2Nx + 255) / 256, 256, 0, s>>>(work, N, L, out);
     return cudaGetLastError();
 }
 

@@ -1,1028 +1,17 @@
-// Monte Carlo photon-packet walk (Sec. 2.1-2.3 of the paper), one persistent
-// kernel per run.
-//
-// Scheduling: a persistent grid (a few CTAs per SM). Each lane owns one
-// packet in registers. Whenever enough lanes of a warp are idle, the warp
-// takes a contiguous block of packet ids with ONE atomicAdd on a global work
-// counter (ballot + popc + shuffle) and the idle lanes emit those packets;
-// this is the server-worker scheme of Sec. 2.3.2 at warp granularity. After
-// the counter runs out, lanes finish their own packets independently.
-//
-// Per iteration a lane advances its packet by one event in the current
-// cell: with x_com = x_lab - n.V/b (Sec. 2.2.1) and alpha = alpha0
-// H(a, x_com) (Sec. 2.1), it either scatters inside the cell (tau < alpha
-// s_exit) or crosses the nearest face. A scattering draws u_par from the
-// velocity sampler (Sec. 2.1.1), u_perp from a Gaussian, an isotropic new
-// direction and x_out = x_in + u_par (g - 1) + u_perp sin(gamma)
-// (Eq. riia-scatter); with probability epsilon (Eq. eps) the photon is
-// destroyed instead. Leaving a non-periodic face is an escape, binned in the
-// lab-frame spectrum.
-//
-// Random numbers: Philox4x32-10 with counter (id_lo, id_hi, event, block)
-// and key (seed_lo, seed_hi); a 32-bit word r becomes ((r >> 9) + 1/2) 2^-23,
-// exact in FP32 and FP64. Event 0 is the emission, event e >= 1 the e-th
-// scattering; the slots of each event are fixed (see emit / scatter), so a
-// packet's stream depends only on (seed, id).
-//
-// Tallies: scattering counts and excitation are summed in registers over a
-// cell visit and flushed with one atomic when the packet leaves the cell;
-// the mean-intensity and emissivity tallies (Eq. scat-line) are added per
-// segment. Spectrum and counters go to FP64 / 64-bit integers.
-//
-// Precision: R = float is the production walk (FP32 arithmetic in cell-local
-// coordinates, so positions keep 2^-24 of a cell width at any optical depth);
-// R = double runs the same steps in FP64 for lockstep checks.
-#include <math.h>
-#include <stdint.h>
-
-#include "krl_internal.cuh"
+// The packet walk for line-profile mode 2 (the Voigt slice; production) and
+// the batched multi-model launch. The walk itself is in transport_impl.cuh;
+// transport_modes.cu instantiates it for modes 1 and 3.
+#include "transport_impl.cuh"
 
 namespace krl {
-
-namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// ---------------------------------------------------------------- Philox4x32-10
-
-struct Words {
-    uint32_t w[4];
-};
-
-__device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const RoundKeys& K)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
-        uint32_t h0 = __umulhi(m0, c0), l0 = m0 * c0;
-        uint32_t h1 = __umulhi(m1, c2), l1 = m1 * c2;
-        uint32_t n0 = h1 ^ c1 ^ K.k[0][r];
-        uint32_t n2 = h0 ^ c3 ^ K.k[1][r];
-        c0 = n0;
-        c1 = l1;
-        c2 = n2;
-        c3 = l0;
-    }
-    return Words{{c0, c1, c2, c3}};
-}
-
-// ---------------------------------------------------------------- precision policy
-
-template <typename R>
-struct Ops;
-
-template <>
-struct Ops<float> {
-    // ((r >> 9) + 1/2) 2^-23 without an int-to-float conversion: the bits
-    // give 1 + (r >> 9) 2^-23, and subtracting 1 - 2^-24 is exact (Sterbenz)
-    static __device__ __forceinline__ float uni(uint32_t r)
-    {
-        return __uint_as_float((r >> 9) + 0x3f800000u) - 0x1.fffffep-1f;
-    }
-    static __device__ __forceinline__ float ln(float v) { return __logf(v); }
-    static __device__ __forceinline__ float ex(float v) { return __expf(v); }
-    // sqrt(v) for v >= 0 as v * rsqrt(v) (one MUFU op, 2 ulp)
-    static __device__ __forceinline__ float sq(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
-    static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
-    // 1/a to about 1 ulp (one MUFU op; used for the exit distances only)
-    static __device__ __forceinline__ float rcp(float a)
-    {
-        float r;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
-        return r;
-    }
-    // sin and cos of 2 pi u for u in (0, 1): shift to [-pi, pi] where the
-    // hardware approximation is accurate, then reflect.
-    static __device__ __forceinline__ void sc2pi(float u, float* s, float* c)
-    {
-        float ss, cc;
-        __sincosf(6.28318530717958648f * (u - 0.5f), &ss, &cc);
-        *s = -ss;
-        *c = -cc;
-    }
-    static __device__ __forceinline__ float big() { return 3.0e38f; }
-    // min(1, max(0, p + d n)): one saturating FMA
-    static __device__ __forceinline__ float step01(float p, float d, float n) { return __saturatef(fmaf(d, n, p)); }
-    // position of |x| on the Voigt table, (log10|x| - L0) (N - 1) / (L1 - L0),
-    // as one FMA on log2|x|
-    static __device__ __forceinline__ float vt(float ax)
-    {
-        constexpr double C = (kVoigtN - 1) / (kVoigtL1 - kVoigtL0);
-        return fmaf(__log2f(ax), (float)(C * 0.30102999566398119521), (float)(-kVoigtL0 * C));
-    }
-};
-
-template <>
-struct Ops<double> {
-    static __device__ __forceinline__ double uni(uint32_t r) { return (double)(r >> 9) * 0x1p-23 + 0x1p-24; }
-    static __device__ __forceinline__ double ln(double v) { return log(v); }
-    static __device__ __forceinline__ double ex(double v) { return exp(v); }
-    static __device__ __forceinline__ double sq(double v) { return sqrt(v); }
-    static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
-    static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
-    static __device__ __forceinline__ void sc2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
-    static __device__ __forceinline__ double big() { return 1.0e300; }
-    static __device__ __forceinline__ double step01(double p, double d, double n) { return fmin(1.0, fmax(0.0, p + d * n)); }
-    static __device__ __forceinline__ double vt(double ax)
-    {
-        return (log10(ax) - (double)kVoigtL0) * ((kVoigtN - 1) / (kVoigtL1 - kVoigtL0));
-    }
-};
-
-// ---------------------------------------------------------------- table lookups (shared memory)
-
-// H(a, x) from the ph_mode 2 slice: ln H linear in log10|x| between nodes.
-// The three ranges are evaluated without branches and the result selected
-// (every path is finite or discarded for any x).
-template <typename R>
-__device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
-{
-    using O = Ops<R>;
-    const R ax = fabs(x);
-    const R t = O::vt(ax);
-    int i = (int)t;
-    i = i < 0 ? 0 : (i > kVoigtN - 2 ? kVoigtN - 2 : i);
-    const R f = t - (R)i;
-    const R l0 = (R)sv[i], l1 = (R)sv[i + 1];
-    const R tab = O::ex(((R)1 - f) * l0 + f * l1);
-    const R ax2 = ax * ax;
-    const R wing = O::dv(a, (R)1.7724538509055160 * ax2) * ((R)1 + O::dv((R)1.5, ax2));
-    return ax < (R)1e-4 ? H0 : (ax > (R)1e3 ? wing : tab);
-}
-
-// Largest row i in [0, 38] with X[i] <= ax: closed-form guess from the node
-// formula, then one fix-up against the stored nodes (the guess is off by at
-// most one). Returns i and the two bracketing nodes.
-template <typename R>
-__device__ __forceinline__ int us_row2(R ax, const float* sx, R& x0, R& x1)
-{
-    // both guesses without a branch (the log one is finite for ax >= 0)
-    const int ilin = (int)(ax * (R)2.25);
-    const int ilog = 18 + (int)((R)21 * Ops<R>::ln(ax * (R)0.125) * (R)0.27588297880498553);  // 1/ln(37.5)
-    int i = ax < (R)8 ? ilin : ilog;
-    i = i < 0 ? 0 : (i > kUsNx - 2 ? kUsNx - 2 : i);
-    x0 = (R)sx[i];
-    x1 = (R)sx[i + 1];
-    while (i > 0 && x0 > ax) {
-        --i;
-        x1 = x0;
-        x0 = (R)sx[i];
-    }
-    while (i < kUsNx - 2 && x1 <= ax) {
-        ++i;
-        x0 = x1;
-        x1 = (R)sx[i + 1];
-    }
-    return i;
-}
-
-// u_par for incoming gas-frame frequency x (|x| <= 300), given L = ln(xi)
-// and the guide bin m of logit(xi). Each bracketing row is inverted at L:
-// the largest node j with c[j] <= L (the guide entry starts at or next to
-// it; the bounded walks make the result exactly the bisection's), then u is
-// linear between nodes j and j + 1; the two rows' u are interpolated in |x|.
-// The two rows are walked together so their shared-memory loads overlap.
-template <typename R>
-__device__ __forceinline__ R us_sample(R x, R L, int m, const float* sx, const float* sc, const unsigned char* sg)
-{
-    using O = Ops<R>;
-    const R ax = fabs(x);
-    R x0, x1;
-    const int i = us_row2(ax, sx, x0, x1);
-    const R t = O::dv(ax - x0, x1 - x0);
-    const float* ra = sc + i * kUsNu;
-    const float* rb = ra + kUsNu;
-    int ja = sg[i * kGuideN + m];
-    int jb = sg[(i + 1) * kGuideN + m];
-    R a0 = (R)ra[ja], a1 = (R)ra[ja + 1];
-    R b0 = (R)rb[jb], b1 = (R)rb[jb + 1];
-    for (;;) {
-        const bool da = ja > 0 && a0 > L;
-        const bool db = jb > 0 && b0 > L;
-        if (!(da || db)) break;
-        if (da) { --ja; a1 = a0; a0 = (R)ra[ja]; }
-        if (db) { --jb; b1 = b0; b0 = (R)rb[jb]; }
-    }
-    for (;;) {
-        const bool ua = ja < kUsNu - 2 && a1 <= L;
-        const bool ub = jb < kUsNu - 2 && b1 <= L;
-        if (!(ua || ub)) break;
-        if (ua) { ++ja; a0 = a1; a1 = (R)ra[ja + 1]; }
-        if (ub) { ++jb; b0 = b1; b1 = (R)rb[jb + 1]; }
-    }
-    const R ua_ = (R)kUsU0 + (R)kUsDu * (R)ja + (R)kUsDu * O::dv(L - a0, a1 - a0);
-    const R ub_ = (R)kUsU0 + (R)kUsDu * (R)jb + (R)kUsDu * O::dv(L - b0, b1 - b0);
-    const R u = ((R)1 - t) * ua_ + t * ub_;
-    return x < (R)0 ? -u : u;
-}
-
-// Guide bin of logit(xi) and L = ln(xi) (< 0 strictly: node 250, ln CDF = 0,
-// always bounds the search).
-template <typename R>
-__device__ __forceinline__ int us_bin(R xi, R& L)
-{
-    using O = Ops<R>;
-    L = fmin(O::ln(xi), (R)-1e-30);
-    const R w = L - O::ln((R)1 - xi);
-    int m = (int)((w + (R)kGuideW) * (R)(kGuideN / (2.0 * kGuideW)));
-    return m < 0 ? 0 : (m > kGuideN - 1 ? kGuideN - 1 : m);
-}
-
-// ---------------------------------------------------------------- packet state
-
-template <typename R>
-struct Pkt {
-    int cx, cy, cz, c;
-    R px, py, pz;
-    R nx, ny, nz;
-    R ix, iy, iz;          // 1 / n
-    R x, tau;
-    float4 rec;            // current cell record
-    uint32_t nscat, ncross, cell0;
-    unsigned long long id;
-    uint32_t vis_scat;     // scatterings in this cell visit
-    R vis_exc;             // sum ds H over this cell visit
-    bool prev_scat;        // last event was a scattering (draw the next one early)
-};
-
-// n . V/b of a cell, always evaluated in this one fixed order (explicit
-// fused multiply-adds): the comoving frequency x_lab - n.V/b then recovers
-// exactly the value that x_lab was built from (e.g. 0 for line-centre
-// emission), whose sign the velocity sampler's symmetry depends on.
-template <typename R>
-__device__ __forceinline__ R vdot(R nx, R ny, R nz, const float4& rec)
-{
-    return fma(nz, (R)rec.w, fma(ny, (R)rec.z, nx * (R)rec.y));
-}
-
-template <typename R>
-__device__ __forceinline__ void set_dir(Pkt<R>& p, R nx, R ny, R nz)
-{
-    p.nx = nx;
-    p.ny = ny;
-    p.nz = nz;
-    if constexpr (sizeof(R) == 4) {
-        // a zero component counts as +1e-30 (the packet then crosses that
-        // face only from exactly on it), so that 1/n is finite and its sign
-        // alone selects the face ahead
-        p.ix = Ops<R>::rcp(nx != 0.0f ? nx : 1e-30f);
-        p.iy = Ops<R>::rcp(ny != 0.0f ? ny : 1e-30f);
-        p.iz = Ops<R>::rcp(nz != 0.0f ? nz : 1e-30f);
-    } else {
-        p.ix = Ops<R>::rcp(nx);
-        p.iy = Ops<R>::rcp(ny);
-        p.iz = Ops<R>::rcp(nz);
-    }
-}
-
-// Distance (in cell widths) to the face ahead along one axis, from the
-// in-cell coordinate q in [0, 1] and the direction component n with 1/n.
-template <typename R>
-__device__ __forceinline__ R face_dist(R q, R n, R in)
-{
-    if constexpr (sizeof(R) == 4) {
-        return fmaf(-q, in, in > 0.0f ? in : 0.0f);      // (1 - q)/n or -q/n
-    } else {
-        return n > 0.0 ? (1.0 - q) * in : (n < 0.0 ? -q * in : 1.0e300);
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void iso_dir(R umu, R uphi, R& nx, R& ny, R& nz)
-{
-    R mu = (R)2 * umu - (R)1;
-    R st = Ops<R>::sq(fmax((R)0, (R)1 - mu * mu));
-    R s, c;
-    Ops<R>::sc2pi(uphi, &s, &c);
-    nx = st * c;
-    ny = st * s;
-    nz = mu;
-}
-
-__device__ __forceinline__ void spectrum_add(const TransportArgs& A, double x)
-{
-    int b;
-    if (x < A.spec_lo) b = 0;
-    else if (x >= A.spec_hi) b = A.spec_n + 1;
-    else {
-        b = 1 + (int)floor((x - A.spec_lo) / (A.spec_hi - A.spec_lo) * A.spec_n);
-        if (b > A.spec_n) b = A.spec_n;
-    }
-    atomicAdd(A.spec_w + b, 1.0);
-    atomicAdd(A.spec_c + b, 1ull);
-}
-
-template <typename R>
-__device__ __forceinline__ void write_record(const TransportArgs& A, const Pkt<R>& p, uint16_t status)
-{
-    if (!A.rec) return;
-    krl_packet_record r;
-    r.x = (float)p.x;
-    r.nscat = p.nscat;
-    r.ncross = p.ncross;
-    r.status = status;
-    r.pad = 0;
-    r.cell0 = p.cell0;
-    A.rec[p.id - A.first] = r;
-}
-
-// Emission (event 0). Slots: block 0 = {mu, phi, tau, freq1},
-// block 1 = {freq2, pos_a, pos_b, pos_c}, block 2 = {cell_hi, cell_lo}.
-// Returns false if the source point lies outside the domain (the packet
-// then leaves at once).
-template <typename R, unsigned F>
-__device__ bool emit(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p)
-{
-    using O = Ops<R>;
-    const uint32_t lo = (uint32_t)p.id, hi = (uint32_t)(p.id >> 32);
-    Words b0 = philox(lo, hi, 0u, 0u, K);
-    const bool need1 = A.src_kind != KRL_SRC_POINT || A.src_profile == KRL_PROFILE_GAUSSIAN;
-    Words b1 = {{0u, 0u, 0u, 0u}};
-    if (need1) b1 = philox(lo, hi, 0u, 1u, K);
-    const int dims[3] = {A.nx, A.ny, A.nz};
-    double X[3];
-    R n[3];
-    if (A.src_kind == KRL_SRC_BEAM) {
-        n[0] = n[1] = n[2] = (R)0;
-        n[A.src_axis] = (R)1;
-        double pos[2] = {(double)O::uni(b1.w[1]), (double)O::uni(b1.w[2])};
-        int q = 0;
-        for (int d = 0; d < 3; ++d) {
-            if (d == A.src_axis) { X[d] = 0.0; continue; }
-            X[d] = (d == A.band_axis) ? A.band_lo + (A.band_hi - A.band_lo) * pos[q] : dims[d] * pos[q];
-            ++q;
-        }
-    } else {
-        iso_dir<R>(O::uni(b0.w[0]), O::uni(b0.w[1]), n[0], n[1], n[2]);
-        if (A.src_kind == KRL_SRC_POINT) {
-            X[0] = A.src_pos[0];
-            X[1] = A.src_pos[1];
-            X[2] = A.src_pos[2];
-        } else if (A.src_kind == KRL_SRC_PLANE) {
-            int q = 1;
-            for (int d = 0; d < 3; ++d)
-                X[d] = (d == A.src_axis) ? A.src_plane : dims[d] * (double)O::uni(b1.w[q++]);
-        } else {
-            Words b2 = philox(lo, hi, 0u, 2u, K);
-            double uc = (double)(b2.w[0] >> 8) * 0x1p-24 + (double)(b2.w[1] >> 8) * 0x1p-48 + 0x1p-49;
-            int l = 0, h = A.ncell - 1;              // first cell with cdf > uc
-            while (l < h) {
-                int m = (l + h) >> 1;
-                if (A.src_cdf[m] > uc) h = m;
-                else l = m + 1;
-            }
-            int cz = l / (A.nx * A.ny);
-            int cy = (l / A.nx) % A.ny;
-            int cx = l % A.nx;
-            X[0] = cx + (double)O::uni(b1.w[1]);
-            X[1] = cy + (double)O::uni(b1.w[2]);
-            X[2] = cz + (double)O::uni(b1.w[3]);
-        }
-    }
-    set_dir(p, n[0], n[1], n[2]);
-    int ci[3];
-    R pp[3];
-    bool inside = true;
-    for (int d = 0; d < 3; ++d) {
-        double f = floor(X[d]);
-        int c = (int)f;
-        double q = X[d] - f;
-        if (q == 0.0 && n[d] < (R)0) {
-            c -= 1;
-            q = 1.0;
-        }
-        if ((A.periodic >> d) & 1u) {
-            c %= dims[d];
-            if (c < 0) c += dims[d];
-        }
-        if (c < 0 || c >= dims[d]) inside = false;
-        ci[d] = c;
-        pp[d] = (R)q;
-    }
-    p.tau = fmax((R)0, -O::ln(O::uni(b0.w[2])));
-    R xcom = (R)0;
-    if (A.src_profile == KRL_PROFILE_GAUSSIAN) {
-        R s, c;
-        O::sc2pi(O::uni(b1.w[0]), &s, &c);
-        xcom = O::sq(fmax((R)0, -O::ln(O::uni(b0.w[3])))) * c;
-    }
-    p.nscat = 0;
-    p.ncross = 0;
-    p.vis_scat = 0;
-    p.vis_exc = (R)0;
-    p.prev_scat = true;
-    if (!inside) {
-        p.x = xcom;
-        p.cell0 = 0xFFFFFFFFu;
-        return false;
-    }
-    p.cx = ci[0];
-    p.cy = ci[1];
-    p.cz = ci[2];
-    p.px = pp[0];
-    p.py = pp[1];
-    p.pz = pp[2];
-    p.c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
-    p.cell0 = (uint32_t)p.c;
-    p.rec = __ldg(A.cells + p.c);
-    R vdn = (F & F_VEL) ? vdot<R>(p.nx, p.ny, p.nz, p.rec) : (R)0;
-    p.x = xcom + vdn;
-    return true;
-}
-
-// Per-segment tallies of the rich mode: mean intensity by comoving channel
-// and the camera-directed emissivity (Eq. scat-line with the trilinear
-// R_IIA table, Eq. riia-table, or Eq. riia-inf for |x_in| >= 120).
-template <typename R, unsigned F>
-__device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xcom, R H)
-{
-    if ((A.rich & KRL_TALLY_J) && A.n_ch > 0) {
-        R q = Ops<R>::dv(-xcom - (R)A.ch_x0, (R)A.ch_dx);
-        if (q >= (R)0 && q < (R)A.n_ch) atomicAdd(A.J + (size_t)p.c * A.n_ch + (int)q, (double)ds);
-    }
-    if (!(A.rich & KRL_TALLY_EMISS) || A.n_ch <= 0) return;
-    const R base = ds * (R)p.rec.x * H * (R)0.079577471545947668;   // 1 / 4 pi
-    const R axc = fabs(xcom);
-    const R sgn = xcom < (R)0 ? (R)-1 : (R)1;    // R(D; -x, g) = R(-D; x, g)
-    for (int m = 0; m < A.n_cam; ++m) {
-        const R cx = (R)A.cam[m][0], cy = (R)A.cam[m][1], cz = (R)A.cam[m][2];
-        R g = p.nx * cx + p.ny * cy + p.nz * cz;
-        g = fmin((R)1, fmax((R)-1, g));
-        R vc = (F & F_VEL) ? vdot<R>(cx, cy, cz, p.rec) : (R)0;
-        // channels with |x_out,k - x_com| <= 10, x_out,k = -(x0 + (k + 1/2) dx) - vc
-        R ctr = Ops<R>::dv(-(R)A.ch_x0 - vc - xcom, (R)A.ch_dx) - (R)0.5;
-        R span = Ops<R>::dv((R)kRdMax, (R)A.ch_dx);
-        int k0 = (int)ceil(ctr - span) - 1;
-        int k1 = (int)floor(ctr + span) + 1;
-        k0 = k0 < 0 ? 0 : k0;
-        k1 = k1 > A.n_ch - 1 ? A.n_ch - 1 : k1;
-        if (k0 > k1) continue;
-        float* out = A.emiss + ((size_t)m * A.ncell + p.c) * A.n_ch;
-        if (axc >= (R)kRxMax) {
-            R v = fmax((R)1 - g, (R)(kRsMin * kRsMin));
-            R inv2v = (R)0.5 / v;
-            R nrm = (R)1 / Ops<R>::sq((R)6.283185307179586 * v);
-            for (int k = k0; k <= k1; ++k) {
-                R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - vc;
-                R D = xo - xcom;
-                if (fabs(D) > (R)kRdMax) continue;
-                atomicAdd(out + k, (float)(base * nrm * Ops<R>::ex(-D * D * inv2v)));
-            }
-            continue;
-        }
-        R fx = axc * (R)((kRnX - 1) / kRxMax);
-        R fg = (g + (R)1) * (R)((kRnG - 1) / 2.0);
-        int j = (int)fx;
-        int kg = (int)fg;
-        j = j > kRnX - 2 ? kRnX - 2 : j;
-        kg = kg > kRnG - 2 ? kRnG - 2 : kg;
-        R wx = fx - (R)j, wg = fg - (R)kg;
-        const float* r00 = A.rtab + ((size_t)kg * kRnX + j) * kRnD;
-        const float* r01 = r00 + kRnD;
-        const float* r10 = r00 + (size_t)kRnX * kRnD;
-        const float* r11 = r10 + kRnD;
-        R w00 = ((R)1 - wg) * ((R)1 - wx), w01 = ((R)1 - wg) * wx;
-        R w10 = wg * ((R)1 - wx), w11 = wg * wx;
-        for (int k = k0; k <= k1; ++k) {
-            R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - vc;
-            R D = xo - xcom;
-            if (fabs(D) > (R)kRdMax) continue;
-            R Dd = sgn * D;
-            R fd = (Dd + (R)kRdMax) * (R)(1.0 / kRdStep);
-            int i = (int)floor(fd);
-            i = i < 0 ? 0 : (i > kRnD - 2 ? kRnD - 2 : i);
-            R wd = fd - (R)i;
-            R a0 = w00 * (R)__ldg(r00 + i) + w01 * (R)__ldg(r01 + i) + w10 * (R)__ldg(r10 + i) + w11 * (R)__ldg(r11 + i);
-            R a1 = w00 * (R)__ldg(r00 + i + 1) + w01 * (R)__ldg(r01 + i + 1) + w10 * (R)__ldg(r10 + i + 1) +
-                   w11 * (R)__ldg(r11 + i + 1);
-            R val = ((R)1 - wd) * a0 + wd * a1;
-            atomicAdd(out + k, (float)(base * val));
-        }
-    }
-}
-
-template <typename R, unsigned F>
-__device__ __forceinline__ void flush_visit(const TransportArgs& A, Pkt<R>& p)
-{
-    if ((F & F_SCAT) && p.vis_scat && A.scat) atomicAdd(A.scat + p.c, (unsigned long long)p.vis_scat);
-    if ((F & F_RICH) && (A.rich & KRL_TALLY_EXC) && p.vis_exc != (R)0) atomicAdd(A.exc + p.c, (double)p.vis_exc);
-    p.vis_scat = 0;
-    p.vis_exc = (R)0;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-// Launch shape per instantiation: the lean FP32 walk runs 512-thread CTAs,
-// two per SM (64 registers each); the FP64 and rich-tally walks need more
-// registers and run 256-thread CTAs.
-template <typename R, unsigned F>
-constexpr int max_block() { return (sizeof(R) == 4 && !(F & F_RICH)) ? 512 : 256; }
-
-// Per-lane event counters (summed over the CTA at the end of a model).
-struct LaneStats {
-    unsigned long long emit, esc, des, stuck, scat, cross;
-};
-
-// ---------------------------------------------------------------- tail compaction
-//
-// Dynamic shared memory after the tables: a control block (the CTA's "ids
-// ran out" flag and per-warp packet counts, double-buffered by round) and a
-// stash that holds one packet per thread, field-major (one 32-bit word per
-// field and slot, so consecutive slots fall in consecutive banks).
-constexpr size_t kCtlOff = (kSmemBytes + 15) / 16 * 16;
-constexpr int kCtlInts = 4 + 2 * 32;
-constexpr size_t kStashOff = kCtlOff + (size_t)kCtlInts * sizeof(int);
-// Events a lane runs between two compaction checks in the tail.
-constexpr int kTailRound = 32;
-
-// Words per stashed packet: cell (c, cx, cy, cz), nscat, ncross, cell0, id
-// (2 words), and px, py, pz, nx, ny, nz, x, tau in R.
-template <typename R>
-constexpr int stash_words() { return 9 + 8 * (int)(sizeof(R) / 4); }
-
-template <typename R, unsigned F>
-constexpr size_t smem_bytes(int block) { return kStashOff + (size_t)stash_words<R>() * 4u * (size_t)block; }
-
-template <typename R>
-__device__ __forceinline__ void put_r(uint32_t* w, int& f, int n, int slot, R v)
-{
-    if constexpr (sizeof(R) == 4) {
-        w[(f++) * n + slot] = __float_as_uint(v);
-    } else {
-        w[(f++) * n + slot] = (uint32_t)__double2loint(v);
-        w[(f++) * n + slot] = (uint32_t)__double2hiint(v);
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ R get_r(const uint32_t* w, int& f, int n, int slot)
-{
-    if constexpr (sizeof(R) == 4) {
-        return __uint_as_float(w[(f++) * n + slot]);
-    } else {
-        const uint32_t lo = w[(f++) * n + slot];
-        const uint32_t hi = w[(f++) * n + slot];
-        return __hiloint2double((int)hi, (int)lo);
-    }
-}
-
-// Moves a packet into / out of stash slot `slot`. The visit tallies are
-// flushed before (they belong to the cell visit, not the packet), and the
-// derived fields (1/n, the cell record) are recomputed from the stored ones
-// by the same functions, so a restored packet continues bit for bit as it
-// would have in its old lane.
-template <typename R>
-__device__ __forceinline__ void stash_put(uint32_t* w, int n, int slot, const Pkt<R>& p)
-{
-    int f = 0;
-    w[(f++) * n + slot] = (uint32_t)p.c;
-    w[(f++) * n + slot] = (uint32_t)p.cx;
-    w[(f++) * n + slot] = (uint32_t)p.cy;
-    w[(f++) * n + slot] = (uint32_t)p.cz;
-    w[(f++) * n + slot] = p.nscat;
-    w[(f++) * n + slot] = p.ncross;
-    w[(f++) * n + slot] = p.cell0;
-    w[(f++) * n + slot] = (uint32_t)p.id;
-    w[(f++) * n + slot] = (uint32_t)(p.id >> 32);
-    put_r<R>(w, f, n, slot, p.px);
-    put_r<R>(w, f, n, slot, p.py);
-    put_r<R>(w, f, n, slot, p.pz);
-    put_r<R>(w, f, n, slot, p.nx);
-    put_r<R>(w, f, n, slot, p.ny);
-    put_r<R>(w, f, n, slot, p.nz);
-    put_r<R>(w, f, n, slot, p.x);
-    put_r<R>(w, f, n, slot, p.tau);
-}
-
-template <typename R>
-__device__ __forceinline__ void stash_get(const TransportArgs& A, const uint32_t* w, int n, int slot, Pkt<R>& p)
-{
-    int f = 0;
-    p.c = (int)w[(f++) * n + slot];
-    p.cx = (int)w[(f++) * n + slot];
-    p.cy = (int)w[(f++) * n + slot];
-    p.cz = (int)w[(f++) * n + slot];
-    p.nscat = w[(f++) * n + slot];
-    p.ncross = w[(f++) * n + slot];
-    p.cell0 = w[(f++) * n + slot];
-    const uint32_t lo = w[(f++) * n + slot];
-    const uint32_t hi = w[(f++) * n + slot];
-    p.id = ((unsigned long long)hi << 32) | lo;
-    p.px = get_r<R>(w, f, n, slot);
-    p.py = get_r<R>(w, f, n, slot);
-    p.pz = get_r<R>(w, f, n, slot);
-    const R nx = get_r<R>(w, f, n, slot);
-    const R ny = get_r<R>(w, f, n, slot);
-    const R nz = get_r<R>(w, f, n, slot);
-    set_dir(p, nx, ny, nz);
-    p.x = get_r<R>(w, f, n, slot);
-    p.tau = get_r<R>(w, f, n, slot);
-    p.rec = __ldg(A.cells + p.c);
-    p.vis_scat = 0;
-    p.vis_exc = (R)0;
-    p.prev_scat = true;
-}
-
-// ---------------------------------------------------------------- one event
-
-// Advances an active packet by one event in its current cell (a scattering
-// inside the cell or a crossing of the nearest face). Returns false when the
-// packet has ended (escape, destruction or event budget).
-template <typename R, unsigned F>
-__device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p, const float* sv,
-                                        const float* sx,
-                                        const float* sc, const unsigned char* sg, R a, R H0, LaneStats& st)
-{
-    using O = Ops<R>;
-    if ((unsigned long long)p.nscat + p.ncross >= A.max_iters) {
-        flush_visit<R, F>(A, p);
-        ++st.stuck;
-        st.scat += p.nscat;
-        st.cross += p.ncross;
-        write_record(A, p, 3);
-        return false;
-    }
-    // Draw the next scattering's random numbers up front, for every lane of
-    // the converged group, when any of them last scattered (the common case
-    // deep in the line core): the lanes then share one pass through Philox
-    // instead of the few lanes that follow a face crossing drawing again in
-    // a divergent branch, and the chains overlap the lookup's latency. A
-    // lane whose event turns out to be a crossing discards its draw.
-    const uint32_t idlo = (uint32_t)p.id, idhi = (uint32_t)(p.id >> 32);
-    Words w0 = {{0u, 0u, 0u, 0u}}, w1 = {{0u, 0u, 0u, 0u}};
-    const bool spec = __any_sync(__activemask(), p.prev_scat);
-    if (spec) {
-        w0 = philox(idlo, idhi, p.nscat + 1u, 0u, K);
-        w1 = philox(idlo, idhi, p.nscat + 1u, 1u, K);
-    }
-    const R vdn = (F & F_VEL) ? vdot<R>(p.nx, p.ny, p.nz, p.rec) : (R)0;
-    const R xcom = p.x - vdn;
-    const R H = voigt<R>(xcom, sv, a, H0);
-    const R alpha = (R)p.rec.x * H;
-    const R tx = face_dist<R>(p.px, p.nx, p.ix);
-    const R ty = face_dist<R>(p.py, p.ny, p.iy);
-    const R tz = face_dist<R>(p.pz, p.nz, p.iz);
-    R sx_ = tx;
-    int axis = 0;
-    if (ty < sx_) { sx_ = ty; axis = 1; }
-    if (tz < sx_) { sx_ = tz; axis = 2; }
-    const bool scat = p.tau < alpha * sx_;
-    const R ds = scat ? O::dv(p.tau, alpha) : sx_;
-    p.px = O::step01(p.px, ds, p.nx);
-    p.py = O::step01(p.py, ds, p.ny);
-    p.pz = O::step01(p.pz, ds, p.nz);
-    if (F & F_RICH) {
-        if (A.rich & KRL_TALLY_EXC) p.vis_exc += ds * H;
-        if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H);
-    }
-    p.prev_scat = scat;
-    if (scat) {
-        // ---- scattering (event e = nscat): block 0 = {u_par, bm_r, bm_phi, tau},
-        //      block 1 = {mu, phi, eps_test, -}
-        ++p.nscat;
-        ++p.vis_scat;
-        if (!spec) {
-            w0 = philox(idlo, idhi, p.nscat, 0u, K);
-            w1 = philox(idlo, idhi, p.nscat, 1u, K);
-        }
-        if ((F & F_RICH) && (A.rich & kRichEps)) {
-            if (O::uni(w1.w[2]) < (R)__ldg(A.eps + p.c)) {
-                flush_visit<R, F>(A, p);
-                ++st.des;
-                st.scat += p.nscat;
-                st.cross += p.ncross;
-                write_record(A, p, 2);
-                return false;
-            }
-        }
-        // independent long-latency work first: Box-Muller, new direction,
-        // the sampler's logs; then the table walk
-        R bs, bc;
-        O::sc2pi(O::uni(w0.w[2]), &bs, &bc);
-        const R rad = O::sq(fmax((R)0, -O::ln(O::uni(w0.w[1]))));
-        R mx, my, mz;
-        iso_dir<R>(O::uni(w1.w[0]), O::uni(w1.w[1]), mx, my, mz);
-        R L;
-        const int gm = us_bin<R>(O::uni(w0.w[0]), L);
-        const R tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
-        const R z1 = rad * bc, z2 = rad * bs;
-        const R us = us_sample<R>(xcom, L, gm, sx, sc, sg);   // finite for any x; unused beyond 300
-        const R upar = fabs(xcom) > (R)300 ? z2 : us;
-        const R g = p.nx * mx + p.ny * my + p.nz * mz;
-        const R sg_ = O::sq(fmax((R)0, (R)1 - g * g));
-        const R xout = xcom + upar * (g - (R)1) + z1 * sg_;
-        set_dir(p, mx, my, mz);
-        const R vdo = (F & F_VEL) ? vdot<R>(mx, my, mz, p.rec) : (R)0;
-        p.x = xout + vdo;
-        p.tau = tau_new;
-        return true;
-    }
-    // ---- cross the face on `axis`
-    p.tau -= alpha * sx_;
-    ++p.ncross;
-    flush_visit<R, F>(A, p);
-    const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
-    const int stride = axis == 0 ? 1 : (axis == 1 ? A.nx : A.nx * A.ny);
-    const int cur = axis == 0 ? p.cx : (axis == 1 ? p.cy : p.cz);
-    // side from the sign of 1/n, which selected the face (see set_dir)
-    const R nd = axis == 0 ? p.ix : (axis == 1 ? p.iy : p.iz);
-    const int step = nd > (R)0 ? 1 : -1;
-    int nc = cur + step;
-    int dc = step * stride;
-    const R pnew = step > 0 ? (R)0 : (R)1;
-    if (axis == 0) p.px = pnew;
-    else if (axis == 1) p.py = pnew;
-    else p.pz = pnew;
-    if (nc < 0 || nc >= dim) {
-        if (!((A.periodic >> axis) & 1u)) {
-            spectrum_add(A, (double)p.x);
-            ++st.esc;
-            st.scat += p.nscat;
-            st.cross += p.ncross;
-            write_record(A, p, 1);
-            return false;
-        }
-        if (nc < 0) { nc += dim; dc += dim * stride; }
-        else { nc -= dim; dc -= dim * stride; }
-    }
-    if (axis == 0) p.cx = nc;
-    else if (axis == 1) p.cy = nc;
-    else p.cz = nc;
-    p.c += dc;
-    p.rec = __ldg(A.cells + p.c);
-    return true;
-}
-
-// One model's walk by the whole CTA: stage the model's tables in shared
-// memory, run packets until the model's id counter is exhausted and every
-// lane has finished, then add the counters. Every thread of the CTA calls it.
-//
-// Bulk phase: each lane owns a packet; a warp refills its idle lanes with one
-// atomic on the id counter (ballot + popc + shuffle). The first warp of the
-// CTA that finds the counter exhausted raises a CTA flag, and every warp
-// leaves the bulk phase at its next iteration.
-//
-// Tail phase (the remaining, typically longest packets): rounds of
-// kTailRound events per lane; after each round the CTA counts its running
-// packets and, if they occupy more warps than they would fill, moves them
-// (through the shared-memory stash) to the lowest threads. Emptied warps
-// then wait at the round barrier without issuing, so the surviving packets
-// run in full warps instead of sharing the issue slots with idle lanes.
-template <typename R, unsigned F>
-__device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKeys& K, float* sm)
-{
-    int* ctl = reinterpret_cast<int*>(reinterpret_cast<char*>(sm) + kCtlOff);
-    uint32_t* stash = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + kStashOff);
-    for (int i = threadIdx.x; i < kVoigtN; i += blockDim.x) sm[kSmemVoigt + i] = A.voigt_lnH[i];
-    for (int i = threadIdx.x; i < kUsNx; i += blockDim.x) sm[kSmemUsX + i] = A.us_x[i];
-    for (int i = threadIdx.x; i < kUsNx * kUsNu; i += blockDim.x) sm[kSmemUsC + i] = A.us_lncdf[i];
-    unsigned char* sgw = reinterpret_cast<unsigned char*>(sm + kSmemFloats);
-    for (int i = threadIdx.x; i < kUsNx * kGuideN; i += blockDim.x) sgw[i] = A.us_guide[i];
-    if (threadIdx.x == 0) ctl[0] = 0;
-    __syncthreads();
-    const float* sv = sm + kSmemVoigt;
-    const float* sx = sm + kSmemUsX;
-    const float* sc = sm + kSmemUsC;
-    const unsigned char* sg = sgw;
-
-    const R a = (R)A.a;
-    const R H0 = (R)__ldg(A.H0);
-    const unsigned lane = threadIdx.x & 31u;
-    const int warp = (int)(threadIdx.x >> 5);
-    const int nwarps = (int)(blockDim.x >> 5);
-    Pkt<R> p;
-    bool active = false;
-    LaneStats st = {0, 0, 0, 0, 0, 0};
-
-    // Both phases run in one loop so that the event code is inlined once.
-    const int n = (int)blockDim.x;
-    bool bulk = true;
-    int round = 0, it = 0;
-    for (;;) {
-        if (bulk) {
-            // ---- bulk phase: refill idle lanes, leave when the ids run out
-            const unsigned idle = __ballot_sync(kFull, !active);
-            const int nidle = __popc(idle);
-            int stop = 0;
-            if (lane == 0) stop = *reinterpret_cast<volatile int*>(ctl);
-            bool leave = __shfl_sync(kFull, stop, 0) != 0;
-            if (!leave && (nidle == 32 || (nidle > 0 && nidle >= A.refill_min))) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(A.next, (unsigned long long)nidle);
-                base = __shfl_sync(kFull, base, 0);
-                leave = base + (unsigned long long)nidle >= A.n;
-                if (leave && lane == 0) *reinterpret_cast<volatile int*>(ctl) = 1;
-                if (!active) {
-                    const unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
-                    if (k < A.n) {
-                        p.id = A.first + k;
-                        ++st.emit;
-                        if (emit<R, F>(A, K, p)) {
-                            active = true;
-                        } else {
-                            spectrum_add(A, (double)p.x);
-                            ++st.esc;
-                            write_record(A, p, 1);
-                        }
-                    }
-                }
-            }
-            if (leave) {                      // warp-uniform; once per warp
-                bulk = false;
-                __syncthreads();
-            }
-        } else if (it == kTailRound || !__any_sync(kFull, active)) {
-            // ---- tail phase, end of a round: count and compact
-            const unsigned m = __ballot_sync(kFull, active);
-            int* cnt = ctl + 4 + 32 * (round & 1);
-            if (lane == 0) cnt[warp] = __popc(m);
-            __syncthreads();
-            int total = 0, before = 0, busy = 0;
-            for (int w = 0; w < nwarps; ++w) {
-                const int c = cnt[w];
-                total += c;
-                before += w < warp ? c : 0;
-                busy += c > 0 ? 1 : 0;
-            }
-            if (total == 0) break;            // CTA-uniform
-            if (busy > (total + 31) / 32) {   // CTA-uniform
-                if (active) {
-                    flush_visit<R, F>(A, p);
-                    stash_put<R>(stash, n, before + __popc(m & ((1u << lane) - 1u)), p);
-                }
-                __syncthreads();
-                // the stash is next written after a later round's count
-                // barrier, which every thread reaches only after this read
-                active = (int)threadIdx.x < total;
-                if (active) stash_get<R>(A, stash, n, (int)threadIdx.x, p);
-            }
-            ++round;
-            it = 0;
-        }
-        if (!bulk) ++it;
-        if (active) active = advance<R, F>(A, K, p, sv, sx, sc, sg, a, H0, st);
-    }
-
-    const unsigned long long tot[6] = {warp_sum(st.emit), warp_sum(st.esc),  warp_sum(st.des),
-                                       warp_sum(st.stuck), warp_sum(st.scat), warp_sum(st.cross)};
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if (tot[k]) atomicAdd(A.stats + k, tot[k]);
-    }
-}
-
-template <typename R, unsigned F>
-__global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport(const __grid_constant__ TransportArgs A)
-{
-    extern __shared__ float sm[];
-    run_model<R, F>(A, A.keys, sm);
-}
-
-// The lowest-numbered model that still has unassigned packet ids, or -1.
-// The shared cursor only moves forward, so the loop ends within n_models
-// steps.
-__device__ int next_model(const BatchArgs& B)
-{
-    int m = atomicAdd(B.cursor, 0);
-    while (m < B.n_models) {
-        const unsigned long long used = atomicAdd(B.models[m].next, 0ull);
-        if (used < B.models[m].n) return m;
-        atomicCAS(B.cursor, m, m + 1);
-        const int m2 = atomicAdd(B.cursor, 0);
-        m = m2 > m ? m2 : m + 1;
-    }
-    return -1;
-}
-
-// Many independent models (grids) in one persistent launch: each CTA takes
-// the lowest model that still has packets, stages that model's tables,
-// runs its warps on it until its ids run out, drains, and takes the next.
-// CTAs finish models at different times, so one model's tail overlaps the
-// next model's bulk instead of idling the device as separate launches do.
-template <typename R, unsigned F>
-__global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport_batch(const __grid_constant__ BatchArgs B)
-{
-    extern __shared__ float sm[];
-    __shared__ TransportArgs sA;
-    __shared__ int s_model;
-    for (;;) {
-        if (threadIdx.x == 0) s_model = next_model(B);
-        __syncthreads();
-        const int m = s_model;
-        if (m < 0) break;
-        {
-            const int* src = reinterpret_cast<const int*>(B.models + m);
-            int* dst = reinterpret_cast<int*>(&sA);
-            for (int i = threadIdx.x; i < (int)(sizeof(TransportArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-        }
-        __syncthreads();
-        run_model<R, F>(sA, B.keys, sm);
-        __syncthreads();     // every warp done before the tables are replaced
-    }
-}
-
-template <typename R, unsigned F>
-cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t s)
-{
-    if (block > max_block<R, F>()) return cudaErrorInvalidConfiguration;
-    auto kern = k_transport<R, F>;
-    static bool configured = false;   // per instantiation, per process
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes<R, F>(max_block<R, F>()));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    kern<<<grid, block, smem_bytes<R, F>(block), s>>>(A);
-    return cudaGetLastError();
-}
-
-template <typename R, unsigned F>
-cudaError_t launch_batch_one(const BatchArgs& B, int grid, int block, cudaStream_t s)
-{
-    if (block > max_block<R, F>()) return cudaErrorInvalidConfiguration;
-    auto kern = k_transport_batch<R, F>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes<R, F>(max_block<R, F>()));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    kern<<<grid, block, smem_bytes<R, F>(block), s>>>(B);
-    return cudaGetLastError();
-}
-
-template <typename R, unsigned F>
-int occupancy_one(int block)
-{
-    if (block > max_block<R, F>()) return 0;
-    auto kern = k_transport<R, F>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<R, F>(max_block<R, F>()));
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem_bytes<R, F>(block)) != cudaSuccess) return 0;
-    return n;
-}
-
-template <typename R>
-cudaError_t dispatch(const TransportArgs& A, unsigned f, int grid, int block, cudaStream_t s)
-{
-    switch (f & 7u) {
-    case 0: return launch_one<R, 0>(A, grid, block, s);
-    case 1: return launch_one<R, 1>(A, grid, block, s);
-    case 2: return launch_one<R, 2>(A, grid, block, s);
-    case 3: return launch_one<R, 3>(A, grid, block, s);
-    case 4: return launch_one<R, 4>(A, grid, block, s);
-    case 5: return launch_one<R, 5>(A, grid, block, s);
-    case 6: return launch_one<R, 6>(A, grid, block, s);
-    default: return launch_one<R, 7>(A, grid, block, s);
-    }
-}
-
-template <typename R>
-cudaError_t dispatch_batch(const BatchArgs& B, unsigned f, int grid, int block, cudaStream_t s)
-{
-    switch (f & 7u) {
-    case 0: return launch_batch_one<R, 0>(B, grid, block, s);
-    case 1: return launch_batch_one<R, 1>(B, grid, block, s);
-    case 2: return launch_batch_one<R, 2>(B, grid, block, s);
-    case 3: return launch_batch_one<R, 3>(B, grid, block, s);
-    case 4: return launch_batch_one<R, 4>(B, grid, block, s);
-    case 5: return launch_batch_one<R, 5>(B, grid, block, s);
-    case 6: return launch_batch_one<R, 6>(B, grid, block, s);
-    default: return launch_batch_one<R, 7>(B, grid, block, s);
-    }
-}
-
-template <typename R>
-int occ_dispatch(unsigned f, int block)
-{
-    switch (f & 7u) {
-    case 0: return occupancy_one<R, 0>(block);
-    case 1: return occupancy_one<R, 1>(block);
-    case 2: return occupancy_one<R, 2>(block);
-    case 3: return occupancy_one<R, 3>(block);
-    case 4: return occupancy_one<R, 4>(block);
-    case 5: return occupancy_one<R, 5>(block);
-    case 6: return occupancy_one<R, 6>(block);
-    default: return occupancy_one<R, 7>(block);
-    }
-}
-
-}  // namespace
 
 cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned features, int grid, int block,
                              cudaStream_t s)
 {
-    return precision == KRL_PREC_FP64 ? dispatch<double>(A, features, grid, block, s)
-                                      : dispatch<float>(A, features, grid, block, s);
+    if (A.ph_mode == 1 || A.ph_mode == 3)
+        return launch_transport_ph(A, A.ph_mode, precision, features, grid, block, s);
+    return precision == KRL_PREC_FP64 ? dispatch<double, 2>(A, features, grid, block, s)
+                                      : dispatch<float, 2>(A, features, grid, block, s);
 }
 
 cudaError_t launch_transport_batch(const BatchArgs& B, int precision, unsigned features, int grid, int block,
@@ -1037,9 +26,11 @@ int transport_max_block(int precision, unsigned features)
     return (precision == KRL_PREC_FP32 && !(features & F_RICH)) ? 512 : 256;
 }
 
-int transport_occupancy(int precision, unsigned features, int block)
+int transport_occupancy(int precision, unsigned features, int block, int ph_mode)
 {
-    return precision == KRL_PREC_FP64 ? occ_dispatch<double>(features, block) : occ_dispatch<float>(features, block);
+    if (ph_mode == 1 || ph_mode == 3) return transport_occupancy_ph(ph_mode, precision, features, block);
+    return precision == KRL_PREC_FP64 ? occ_dispatch<double, 2>(features, block)
+                                      : occ_dispatch<float, 2>(features, block);
 }
 
 }  // namespace krl

@@ -1,0 +1,26 @@
+// The packet walk instantiated for line-profile modes 1 (two-dimensional
+// Voigt table and sampler in global memory) and 3 (core-wing blend),
+// Sec. 2.3.1. A translation unit of its own so that it compiles in parallel
+// with the production walk.
+#include "transport_impl.cuh"
+
+namespace krl {
+
+cudaError_t launch_transport_ph(const TransportArgs& A, int ph_mode, int precision, unsigned features, int grid,
+                                int block, cudaStream_t s)
+{
+    const bool d = precision == KRL_PREC_FP64;
+    if (ph_mode == 1) return d ? dispatch<double, 1>(A, features, grid, block, s) : dispatch<float, 1>(A, features, grid, block, s);
+    if (ph_mode == 3) return d ? dispatch<double, 3>(A, features, grid, block, s) : dispatch<float, 3>(A, features, grid, block, s);
+    return cudaErrorInvalidValue;
+}
+
+int transport_occupancy_ph(int ph_mode, int precision, unsigned features, int block)
+{
+    const bool d = precision == KRL_PREC_FP64;
+    if (ph_mode == 1) return d ? occ_dispatch<double, 1>(features, block) : occ_dispatch<float, 1>(features, block);
+    if (ph_mode == 3) return d ? occ_dispatch<double, 3>(features, block) : occ_dispatch<float, 3>(features, block);
+    return 0;
+}
+
+}  // namespace krl

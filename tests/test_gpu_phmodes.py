@@ -1,0 +1,151 @@
+"""Line-profile modes 1 (two-dimensional Voigt table and sampler in global
+memory) and 3 (core-wing blend), Sec. 2.3.1, on the device: the table
+against the oracle's, FP64 lockstep against the oracle's walk, the FP32 walk
+statistically, and the paper's damped-slab sweep (Sec. 3.1: a = 0.149, mean
+depths 200 ... 32000, 1e5 packets) against the Neufeld peak scaling
+x_peak = 0.881 (a tau_m)^{1/3}, with modes 1 and 2 consistent."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import tables as OT
+from _gpu_common import agreement, chi2_two_sample, gpu_run, need_gpu, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+def _mode(p, m):
+    return dataclasses.replace(p, line=dataclasses.replace(p.line, ph_mode=m))
+
+
+def _e1_slab(tau_m, n_packets, bins=(-40.0, 40.0, 1600)):
+    """The paper's slab: 128 cells across (transverse periodic), central
+    plane source of line-centre photons, a = 0.149; mean depth tau_m =
+    sqrt(pi) x the line-centre depth used by the workload."""
+    return W.slab(tau0=tau_m / math.sqrt(math.pi), a=0.149, nz=128, n_packets=n_packets, bins=bins)
+
+
+def test_voigt2d_table_matches_oracle():
+    krl = need_gpu()
+    p = _mode(W.slab(tau0=100.0, n_packets=10), 1)
+    g = krl.Grid(p)
+    try:
+        tab = g.tally("voigt2d").cpu().numpy().reshape(64, 512)
+    finally:
+        g.close()
+    ref = OT.voigt2d_table()
+    assert np.allclose(tab, ref, rtol=3e-7, atol=1e-7)
+
+
+def _lockstep_cases():
+    return {
+        "e1_slab": _e1_slab(2000.0, 1000, bins=(-20.0, 20.0, 200)),
+        "sphere_outflow": W.sphere(vmax_kms=200.0, tau0=1e4, n=16, n_packets=1000),
+        "box_volume_exc": W.box(tau0=100.0, n=8, n_packets=2000, tallies=("scatmap", "exc")),
+    }
+
+
+LOCK = _lockstep_cases()
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("name", list(LOCK))
+def test_lockstep(mode, name):
+    krl = need_gpu()
+    p = _mode(LOCK[name], mode)
+    gpu = gpu_run(krl, p, krl.KRL_PREC_FP64)
+    ref = oracle.run(p, records=True)
+    gr, rr = gpu["records"], ref["records"]
+    # status, scatterings and emission cell on the lockstep bar; face
+    # crossings equal but for pairs: where a scattering point falls within
+    # rounding of a periodic face (the slab's one-cell transverse axes), one
+    # walk wraps across and back (+2 crossings) and nothing else changes
+    ok = agreement(gr, rr, strict=False) & (gr["cell0"] == rr["cell0"])
+    assert ok.mean() >= 0.999, (name, mode, int((~ok).sum()))
+    dcross = gr["ncross"].astype(np.int64) - rr["ncross"].astype(np.int64)
+    assert np.mean(dcross == 0) >= 0.99 and np.all(dcross[ok] % 2 == 0), (name, mode, dcross[dcross != 0])
+    dx = np.abs(gpu["records"]["x"][ok].astype(np.float64) - ref["records"]["x"][ok])
+    assert np.mean(dx <= 2e-6 * np.maximum(1.0, np.abs(ref["records"]["x"][ok]))) >= 0.99
+    nbad = int((~ok).sum())
+    dc = np.abs(gpu["spec_n"].astype(np.int64) - ref["spec_c"].astype(np.int64))
+    assert dc.sum() <= 2 * nbad
+    if ref["exc"] is not None and nbad == 0:
+        assert np.allclose(gpu["exc"], ref["exc"], rtol=1e-9, atol=1e-12 * max(1.0, ref["exc"].max()))
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+def test_fp32_walk_against_oracle(mode):
+    krl = need_gpu()
+    p = _mode(_e1_slab(2000.0, 20000, bins=(-20.0, 20.0, 80)), mode)
+    gpu = gpu_run(krl, p, krl.KRL_PREC_FP32)
+    ref = oracle.run(p, records=True)
+    ok = agreement(gpu["records"], ref["records"], strict=False)
+    assert ok.mean() > 0.9, ok.mean()
+    g, r = gpu["spec_n"][1:-1], ref["spec_c"][1:-1]
+    assert rel_l1(g, r) < 0.03, rel_l1(g, r)
+    assert chi2_two_sample(g, r)[2] > 0.01
+
+
+def _x_peak(spec, lo, hi, guess):
+    """Peak of the escaped spectrum folded to |x|: the histogram smoothed
+    with a Gaussian of width 0.1 guess, then a parabola through the
+    largest smoothed bin and its neighbours."""
+    c = np.asarray(spec, dtype=np.float64)
+    n = c.size
+    edges = np.linspace(lo, hi, n + 1)
+    xc = 0.5 * (edges[1:] + edges[:-1])
+    dx = edges[1] - edges[0]
+    pos = xc > 0
+    folded = c[pos] + c[~pos][::-1]
+    xs = xc[pos]
+    sig = 0.1 * guess / dx
+    k = np.arange(-int(4 * sig) - 1, int(4 * sig) + 2)
+    ker = np.exp(-0.5 * (k / sig) ** 2)
+    sm = np.convolve(folded, ker / ker.sum(), mode="same")
+    i = int(np.argmax(sm[1:-1])) + 1
+    y0, y1, y2 = sm[i - 1], sm[i], sm[i + 1]
+    den = y0 - 2 * y1 + y2
+    off = 0.5 * (y0 - y2) / den if den != 0 else 0.0
+    return xs[i] + off * dx
+
+
+def test_neufeld_sweep_all_modes():
+    """Sec. 3.1's sweep through all three modes. The exact modes follow
+    x_peak = 0.881 (a tau_m)^{1/3} within a few per cent where a tau_m is
+    large and agree with each other at the 1-2% level; the blend is only
+    reported (the paper offers it as a demonstration)."""
+    krl = need_gpu()
+    taus = [200.0, 500.0, 2000.0, 8000.0, 32000.0]
+    res = {}
+    for tau_m in taus:
+        pred = 0.881 * (0.149 * tau_m) ** (1.0 / 3.0)
+        for m in (1, 2, 3):
+            p = _mode(_e1_slab(tau_m, 100_000), m)
+            out = gpu_run(krl, p, krl.KRL_PREC_FP32, records=False, tallies=True)
+            s = out["stats"]
+            assert s.emitted == 100_000 == s.escaped
+            res[(tau_m, m)] = _x_peak(out["spec_n"][1:-1], -40.0, 40.0, pred) / pred
+    print("x_peak / 0.881 (a tau_m)^(1/3):",
+          {f"{t:g}": [round(res[(t, m)], 4) for m in (1, 2, 3)] for t in taus})
+    for t in taus:
+        for m in (1, 2):
+            tol = 0.05 if 0.149 * t >= 250 else 0.12
+            assert abs(res[(t, m)] - 1.0) < tol, (t, m, res[(t, m)])
+        assert abs(res[(t, 1)] / res[(t, 2)] - 1.0) < 0.03, (t, res[(t, 1)], res[(t, 2)])
+
+
+def test_modes_rejected_where_unsupported():
+    krl = need_gpu()
+    with pytest.raises(krl.KrlError):           # a outside the 2-D table
+        g = krl.Grid(_mode(W.slab(tau0=100.0, a=1e-8, n_packets=10), 1))
+        g.close()
+    g = krl.Grid(_mode(W.slab(tau0=100.0, n_packets=10), 3))
+    try:
+        with pytest.raises(krl.KrlError):       # the batch runs mode 2 only
+            krl.Batch([g])
+    finally:
+        g.close()
