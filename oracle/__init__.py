@@ -31,7 +31,10 @@ _LIB = os.path.join(_HERE, "_liborc.so")
 TALLY_BITS = {"scatmap": 1, "exc": 2, "J": 4, "emiss": 8}
 SRC_KIND = {"point": 0, "plane": 1, "beam": 2, "volume": 3}
 PROFILE = {"line_centre": 0, "gaussian": 1}
-ESCAPED, DESTROYED, STUCK = 1, 2, 3
+ESCAPED, DESTROYED, STUCK, ABSORBED = 1, 2, 3, 4
+# A packet whose weight falls below this (after continuum absorption) ends
+# as absorbed (reading: the paper does not say how weights are cut off).
+WEIGHT_CUT = 1e-12
 
 
 def build(force: bool = False) -> str:
@@ -62,6 +65,7 @@ class _Problem(C.Structure):
         ("n_cam", C.c_int), ("cam_dir", C.POINTER(C.c_double)),
         ("tally_flags", C.c_uint), ("max_iters", C.c_uint64),
         ("ph_mode", C.c_int), ("voigt2d", C.POINTER(C.c_double)), ("u0", C.c_double),
+        ("tau_abs", C.POINTER(C.c_double)), ("wcut", C.c_double),
     ]
 
 
@@ -74,6 +78,7 @@ class _Tallies(C.Structure):
         ("spec_w", C.POINTER(C.c_double)), ("spec_c", C.POINTER(C.c_uint64)),
         ("scat", C.POINTER(C.c_uint64)), ("exc", C.POINTER(C.c_double)),
         ("J", C.POINTER(C.c_double)), ("emiss", C.POINTER(C.c_double)),
+        ("absw", C.POINTER(C.c_double)),
         ("stats", C.c_uint64 * 8), ("rec", C.c_void_p),
     ]
 
@@ -143,6 +148,9 @@ def derive(problem):
     if ln.k_ul > 0 and problem.n_coll is not None:
         e = T.epsilon(ln.k_ul, np.asarray(problem.n_coll, dtype=np.float64).reshape(-1), ln.A_ul)
         eps = e.astype(np.float32).astype(np.float64)
+    tau_abs = None
+    if getattr(problem, "tau_abs", None) is not None:
+        tau_abs = np.asarray(problem.tau_abs, dtype=np.float32).astype(np.float64).reshape(-1)
     cdf = None
     if problem.source.kind == "volume":
         r = np.asarray(problem.source.rate, dtype=np.float32).astype(np.float64).reshape(-1)
@@ -152,7 +160,7 @@ def derive(problem):
     if problem.cameras:
         cams = np.array([[math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)]
                          for t, p in problem.cameras], dtype=np.float64)
-    return {"b": b, "a": a, "tau0": tau0, "vel": vel, "eps": eps, "cdf": cdf, "cam": cams}
+    return {"b": b, "a": a, "tau0": tau0, "vel": vel, "eps": eps, "cdf": cdf, "cam": cams, "tau_abs": tau_abs}
 
 
 def run(problem, n: int | None = None, first: int = 0, seed: int | None = None,
@@ -161,9 +169,10 @@ def run(problem, n: int | None = None, first: int = 0, seed: int | None = None,
     """Run packets [first, first+n) of `problem` through the FP64 walk.
 
     Returns a dict: spec_w, spec_c (under, bins, over), scat, exc, J, emiss
-    (raw sums with unit packet weight, lengths in cell widths), stats
-    (emitted, escaped, destroyed, stuck, scatterings, crossings), records,
-    and the derived b, a."""
+    (raw sums with unit packet weight, lengths in cell widths), absw (weight
+    absorbed by the continuum per cell, when the problem has tau_abs), stats
+    (emitted, escaped, destroyed, stuck, scatterings, crossings, absorbed),
+    records, and the derived b, a."""
     n = problem.n_packets if n is None else int(n)
     seed = problem.seed if seed is None else int(seed)
     d = derive(problem)
@@ -209,6 +218,10 @@ def run(problem, n: int | None = None, first: int = 0, seed: int | None = None,
         P.voigt2d = _dp(v2)
     elif ph == 3:
         P.u0 = T.blend_u0(float(d["a"]))
+    if d["tau_abs"] is not None:
+        keep.append(d["tau_abs"])
+        P.tau_abs = _dp(d["tau_abs"])
+    P.wcut = WEIGHT_CUT
     ncam = max(1, len(problem.cameras))
     out = {
         "spec_w": np.zeros(problem.spectrum[2] + 2), "spec_c": np.zeros(problem.spectrum[2] + 2, np.uint64),
@@ -217,12 +230,14 @@ def run(problem, n: int | None = None, first: int = 0, seed: int | None = None,
         "J": np.zeros(ncell * max(nch, 1)) if flags & 4 else None,
         "emiss": np.zeros(ncam * ncell * max(nch, 1)) if flags & 8 else None,
         "records": np.zeros(n, RECORD_DTYPE) if records else None,
+        "absw": np.zeros(ncell) if d["tau_abs"] is not None else None,
     }
     Tl = _Tallies()
     Tl.spec_w = _dp(out["spec_w"])
     Tl.spec_c = out["spec_c"].ctypes.data_as(C.POINTER(C.c_uint64))
     Tl.scat = out["scat"].ctypes.data_as(C.POINTER(C.c_uint64)) if out["scat"] is not None else None
     Tl.exc, Tl.J, Tl.emiss = _dp(out["exc"]), _dp(out["J"]), _dp(out["emiss"])
+    Tl.absw = _dp(out["absw"])
     Tl.rec = out["records"].ctypes.data if records else None
     nthreads = nthreads or os.cpu_count() or 1
     rc = _lib().orc_run(C.byref(P), first, n, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF,

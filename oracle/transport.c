@@ -19,7 +19,11 @@
  *   per-segment tallies: excitation (Sec. 2.1.3 pumping rate), comoving
  *     channel path length (mean intensity), camera-directed scattering
  *     emissivity (Eq. scat-line with Eq. riia-table / riia-inf),
- *   escape into the lab-frame spectrum (Sec. 2.3.2).
+ *   continuum (dust) absorption: the packet weight decays as exp(-dtau_e)
+ *     along each segment and the segment's tallies take the mean weight
+ *     (1 - exp(-dtau_e))/dtau_e (Eq. scat-line); the absorbed weight is
+ *     tallied per cell and a packet below the weight cut ends as absorbed,
+ *   escape into the lab-frame spectrum (Sec. 2.3.2) with the packet weight.
  *
  * Precision model: the per-cell fields and the tables arrive already
  * rounded to float32 (the method stores them in single precision, Sec. 2.3);
@@ -46,7 +50,7 @@
 enum { ORC_SRC_POINT = 0, ORC_SRC_PLANE = 1, ORC_SRC_BEAM = 2, ORC_SRC_VOLUME = 3 };
 enum { ORC_PROFILE_LINE_CENTRE = 0, ORC_PROFILE_GAUSSIAN = 1 };
 enum { ORC_T_SCATMAP = 1, ORC_T_EXC = 2, ORC_T_J = 4, ORC_T_EMISS = 8 };
-enum { ORC_ESCAPED = 1, ORC_DESTROYED = 2, ORC_STUCK = 3 };
+enum { ORC_ESCAPED = 1, ORC_DESTROYED = 2, ORC_STUCK = 3, ORC_ABSORBED = 4 };
 
 /* table geometry (fixed by the readings in oracle/tables.py) */
 #define V_N 5000
@@ -96,6 +100,8 @@ typedef struct {
     int ph_mode;             /* 2: the 1-D slice; 1: the 2-D table; 3: core-wing blend */
     const double* voigt2d;   /* [64][512] ln H for ph_mode 1 */
     double u0;               /* core-wing crossing point for ph_mode 3 */
+    const double* tau_abs;   /* [ncell] continuum absorption optical depth per cell width, or NULL */
+    double wcut;             /* a packet whose weight falls below this is absorbed */
 } orc_problem;
 
 typedef struct {
@@ -113,7 +119,9 @@ typedef struct {
     double* exc;             /* [ncell]     sum of w ds H(a, x_com) */
     double* J;               /* [ncell][n_ch] sum of w ds in the comoving channel of x_com */
     double* emiss;           /* [n_cam][ncell][n_ch] */
-    uint64_t stats[8];       /* emitted, escaped, destroyed, stuck, scatterings, crossings */
+    double* absw;            /* [ncell] packet weight absorbed by the continuum */
+    uint64_t stats[8];       /* emitted, escaped, destroyed, stuck, scatterings, crossings,
+                                absorbed (weight below wcut) */
     orc_record* rec;         /* [n] or NULL */
 } orc_tallies;
 
@@ -334,19 +342,32 @@ static void add_spectrum(const orc_problem* P, orc_tallies* T, double x, double 
     T->spec_c[b] += 1;
 }
 
+/* Continuum absorption over a segment of optical depth dt (Sec. 2.2.1,
+ * Eq. scat-line): the packet weight decays as exp(-dt); the segment's
+ * tallies take the weight at its start times (1 - exp(-dt)) / dt, the mean
+ * weight along it (evaluated as -expm1(-dt)/dt, and by its series below
+ * dt = 1e-4). Returns that factor and the absorbed fraction 1 - exp(-dt). */
+static double segment_factor(double dt, double* absorbed)
+{
+    *absorbed = -expm1(-dt);
+    if (dt < 1e-4) return 1.0 - dt * (0.5 - dt * (1.0 / 6.0 - dt / 24.0));
+    return *absorbed / dt;
+}
+
 static void tally_segment(const orc_problem* P, orc_tallies* T, size_t c, const orc_packet* k,
-                          double ds, double xcom, double H)
+                          double ds, double xcom, double H, double fseg)
 {
     unsigned f = P->tally_flags;
     size_t ncell = (size_t)P->nx * P->ny * P->nz;
-    if (f & ORC_T_EXC) T->exc[c] += k->w * ds * H;
+    const double w = k->w * fseg;
+    if (f & ORC_T_EXC) T->exc[c] += w * ds * H;
     if ((f & ORC_T_J) && P->n_ch > 0) {
         /* comoving channel of x_com: velocity v = -x b, k = floor((v - vmin) / dv) */
         double q = (-xcom - P->ch_x0) / P->ch_dx;
-        if (q >= 0.0 && q < P->n_ch) T->J[c * P->n_ch + (size_t)floor(q)] += k->w * ds;
+        if (q >= 0.0 && q < P->n_ch) T->J[c * P->n_ch + (size_t)floor(q)] += w * ds;
     }
     if ((f & ORC_T_EMISS) && P->n_ch > 0) {
-        double base = k->w * ds * P->tau0[c] * H / (4.0 * ORC_PI);
+        double base = w * ds * P->tau0[c] * H / (4.0 * ORC_PI);
         for (int m = 0; m < P->n_cam; ++m) {
             const double* nc = P->cam_dir + 3 * m;
             double g = k->n[0] * nc[0] + k->n[1] * nc[1] + k->n[2] * nc[2];
@@ -452,7 +473,14 @@ static void run_packet(const orc_problem* P, uint64_t id, uint32_t k0, uint32_t 
             /* scattering inside this cell */
             double s = k.tau / alpha;
             for (int d = 0; d < 3; ++d) k.p[d] = fmin(1.0, fmax(0.0, k.p[d] + s * k.n[d]));
-            tally_segment(P, T, c, &k, s, xcom, H);
+            double fseg = 1.0, fabs_ = 0.0;
+            if (P->tau_abs) fseg = segment_factor(P->tau_abs[c] * s, &fabs_);
+            tally_segment(P, T, c, &k, s, xcom, H, fseg);
+            if (P->tau_abs) {
+                T->absw[c] += k.w * fabs_;
+                k.w *= 1.0 - fabs_;
+                if (k.w < P->wcut) { status = ORC_ABSORBED; break; }
+            }
             ++nscat;
             if (P->tally_flags & ORC_T_SCATMAP) T->scat[c] += 1;
             double u0[4], u1[4];
@@ -478,7 +506,14 @@ static void run_packet(const orc_problem* P, uint64_t id, uint32_t k0, uint32_t 
                 if (d == axis) continue;
                 k.p[d] = fmin(1.0, fmax(0.0, k.p[d] + s_exit * k.n[d]));
             }
-            tally_segment(P, T, c, &k, s_exit, xcom, H);
+            double fseg = 1.0, fabs_ = 0.0;
+            if (P->tau_abs) fseg = segment_factor(P->tau_abs[c] * s_exit, &fabs_);
+            tally_segment(P, T, c, &k, s_exit, xcom, H, fseg);
+            if (P->tau_abs) {
+                T->absw[c] += k.w * fabs_;
+                k.w *= 1.0 - fabs_;
+                if (k.w < P->wcut) { status = ORC_ABSORBED; break; }
+            }
             ++ncross;
             int step = k.n[axis] > 0.0 ? 1 : -1;
             int nc = k.ci[axis] + step;
@@ -493,6 +528,7 @@ static void run_packet(const orc_problem* P, uint64_t id, uint32_t k0, uint32_t 
 done:
     if (status == ORC_ESCAPED) T->stats[1] += 1;
     else if (status == ORC_DESTROYED) T->stats[2] += 1;
+    else if (status == ORC_ABSORBED) T->stats[6] += 1;
     else T->stats[3] += 1;
     T->stats[4] += nscat;
     T->stats[5] += ncross;
@@ -530,11 +566,12 @@ static void tallies_alloc(const orc_problem* P, orc_tallies* T)
     if (f & ORC_T_EMISS)
         T->emiss = calloc((size_t)(P->n_cam > 0 ? P->n_cam : 1) * ncell * (size_t)(P->n_ch > 0 ? P->n_ch : 1),
                           sizeof(double));
+    if (P->tau_abs) T->absw = calloc(ncell, sizeof(double));
 }
 
 static void tallies_free(orc_tallies* T)
 {
-    free(T->spec_w); free(T->spec_c); free(T->scat); free(T->exc); free(T->J); free(T->emiss);
+    free(T->spec_w); free(T->spec_c); free(T->scat); free(T->exc); free(T->J); free(T->emiss); free(T->absw);
 }
 
 /*
@@ -575,6 +612,7 @@ int orc_run(const orc_problem* P, uint64_t first, uint64_t n, uint32_t seed_lo, 
         for (int b = 0; b < P->spec_n + 2; ++b) { out->spec_w[b] += T->spec_w[b]; out->spec_c[b] += T->spec_c[b]; }
         if (f & ORC_T_SCATMAP) for (size_t c = 0; c < ncell; ++c) out->scat[c] += T->scat[c];
         if (f & ORC_T_EXC) for (size_t c = 0; c < ncell; ++c) out->exc[c] += T->exc[c];
+        if (P->tau_abs && out->absw) for (size_t c = 0; c < ncell; ++c) out->absw[c] += T->absw[c];
         if (f & ORC_T_J) for (size_t c = 0; c < ncell * (size_t)P->n_ch; ++c) out->J[c] += T->J[c];
         if (f & ORC_T_EMISS)
             for (size_t c = 0; c < (size_t)P->n_cam * ncell * (size_t)P->n_ch; ++c) out->emiss[c] += T->emiss[c];

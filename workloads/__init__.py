@@ -17,6 +17,7 @@ Workloads (shapes follow the paper's validation and application setups):
                   (static, outflow or infall) and a central point source.
 * ``thin_slab`` - optically thin moving slab lit by an in-plane beam and seen
                   face-on (Sec. 3.3, Eq. thin-slab).
+* ``dusty_slab`` - the slab with uniform continuum absorption (Sec. 3.2).
 * ``box``       - uniform cube with a volume source and thermal emission
                   profile (Sec. 3.5.2, Table 1 setup).
 * ``envelope``  - rotating, infalling envelope with an inner cavity and
@@ -86,6 +87,8 @@ class Problem:
     source: Source
     vel_cms: Optional[np.ndarray] = None    # float32 [3, nz, ny, nx] (vx, vy, vz) [cm/s]
     n_coll: Optional[np.ndarray] = None     # float32 [nz, ny, nx] collider density [cm^-3]
+    tau_abs: Optional[np.ndarray] = None    # float32 [nz, ny, nx] continuum (dust) absorption
+                                            # optical depth per cell width
     spectrum: tuple = (-30.0, 30.0, 200)    # escaped spectrum bins in x: (lo, hi, n)
     channels: Optional[tuple] = None        # (v_min [cm/s], dv [cm/s], n_ch)
     cameras: tuple = ()                     # ((theta, phi), ...) in radians
@@ -143,6 +146,18 @@ def sphere(vmax_kms: float = 0.0, tau0: float = 1e6, a: float = 4.7e-4, n: int =
         line=Line(LYA_NU0_HZ, HYDROGEN_AMU, LYA_A_UL, 6.0, 2.0, 0.0, a),
         source=Source(SOURCE_POINT, pos=(R, R, R), profile=PROFILE_LINE_CENTRE),
         vel_cms=vel, spectrum=bins, tallies=tallies, n_packets=n_packets, seed=seed)
+
+
+def dusty_slab(tau_a: float, tau0: float = 1e5, a: float = 0.015, nz: int = 64, n_packets: int = 200_000,
+               seed: int = 0, bins: tuple = (-60.0, 60.0, 240), tallies: tuple = ()) -> Problem:
+    """Static slab with uniform continuum (dust) absorption (Sec. 3.2): T =
+    10 K (a = 0.015 for the resonance line), line-centre depth tau0 and
+    absorption depth tau_a from the midplane to a face, a central plane of
+    line-centre photons, transverse axes periodic."""
+    p = slab(tau0=tau0, a=a, nz=nz, n_packets=n_packets, seed=seed, T_K=10.0, bins=bins, tallies=tallies)
+    p.name = f"dusty_slab_tau{tau0:g}_a{a:g}_taua{tau_a:g}"
+    p.tau_abs = np.full(p.shape, tau_a / (nz / 2), dtype=np.float32)
+    return p
 
 
 def box(tau0: float = 1e3, a: float = 4.73e-3, n: int = 32, T_K: float = 100.0,
