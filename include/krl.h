@@ -82,6 +82,13 @@ typedef struct {
     const float* vy;
     const float* vz;
     const float* n_coll;        /* device collider density [cm^-3] or NULL (Eq. eps) */
+    const float* tau_abs;       /* device continuum (dust) absorption optical depth per
+                                   cell width, >= 0, or NULL. The packet weight decays
+                                   as exp(-tau_abs ds) along each segment and the
+                                   segment's tallies take the mean weight
+                                   (1 - exp(-dtau))/dtau (Eq. scat-line); the ray
+                                   trace adds it to the line opacity. A packet whose
+                                   weight falls below 1e-12 ends as absorbed.      */
 } krl_grid_desc;
 
 typedef struct krl_grid krl_grid;
@@ -194,13 +201,15 @@ typedef struct {
     float x;                    /* lab-frame x at escape / destruction             */
     uint32_t nscat;             /* scatterings                                     */
     uint32_t ncross;            /* cell-face crossings                             */
-    uint16_t status;            /* 1 escaped, 2 destroyed, 3 budget exhausted       */
+    uint16_t status;            /* 1 escaped, 2 destroyed, 3 budget exhausted,
+                                   4 absorbed (weight below the cut)                */
     uint16_t pad;
     uint32_t cell0;             /* flat index of the emission cell                 */
 } krl_packet_record;
 
 typedef struct {
     uint64_t emitted, escaped, destroyed, stuck, scatterings, crossings;
+    uint64_t absorbed;          /* packets whose weight fell below the cut          */
 } krl_run_stats;
 
 /*
@@ -222,7 +231,8 @@ KRL_API krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, u
 /* ------------------------------------------------------------------ tallies */
 
 typedef enum {
-    KRL_OUT_SPEC_W = 0,   /* double [spec_nbins + 2]: under, bins, over (weights)   */
+    KRL_OUT_SPEC_W = 0,   /* double [spec_nbins + 2]: under, bins, over (escaped
+                             packet weights)                                       */
     KRL_OUT_SPEC_N = 1,   /* uint64 [spec_nbins + 2]: packet counts               */
     KRL_OUT_SCATMAP = 2,  /* uint64 [ncell]: scatterings per cell                  */
     KRL_OUT_EXC = 3,      /* double [ncell]: sum of w ds H(a, x_com) (ds in cells)  */
@@ -230,7 +240,10 @@ typedef enum {
     KRL_OUT_EMISS = 5,    /* float [n_cam][ncell][n_ch]: sum of
                              w ds alpha0 H(a,x_in) R(x_out,k; x_in, g) / 4 pi      */
     KRL_OUT_STATS = 6,    /* uint64 [8]: emitted, escaped, destroyed, stuck,
-                             scatterings, crossings, 0, 0 (all runs since reset)   */
+                             scatterings, crossings, absorbed, 0 (all runs since
+                             reset)                                                */
+    KRL_OUT_ABSW = 7,     /* double [ncell]: packet weight absorbed by the continuum
+                             (grids with tau_abs)                                  */
     /* read-only views of what krl_line_set built (float32 unless noted) */
     KRL_OUT_VOIGT = 16,   /* [5000]: ln H(a, 10^l), l = -4 + 7 i / 4999           */
     KRL_OUT_US_X = 17,    /* [40]: sampler incoming-frequency nodes |x|           */

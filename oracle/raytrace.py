@@ -10,13 +10,15 @@ centred on the box centre, width fov cells, I_in = 0 where the ray enters.
 Per cell segment of length dl and channel k with gas-frame frequency
 x_k = -(v_k / b) - n_cam . V / b:
 
-    alpha_k = alpha0 H(a, x_k),   dtau = alpha_k dl,
+    alpha_k = alpha0 H(a, x_k) + alpha_abs,   dtau = alpha_k dl,
     I_out = I_in exp(-dtau) + S_k (1 - exp(-dtau)),
     S_k = (j_sca,k + j_line H(a, x_k) / sqrt(pi)) / alpha_k,
 
 written as I_out = I_in e^{-dtau} + j_k dl (1 - e^{-dtau}) / dtau so that
-an empty cell (alpha = 0) adds j dl. The cell walk is the oracle's own
-(orc_trace in transport.c).
+an empty cell (alpha = 0) adds j dl. alpha_abs is the continuum absorption
+(zero without one): the two-step scheme applies it in this formal solution
+(Sec. 3.2), the continuum adding extinction but no emission. The cell walk
+is the oracle's own (orc_trace in transport.c).
 """
 from __future__ import annotations
 
@@ -77,6 +79,7 @@ def trace_maps(oracle_mod, problem, emiss, camera: int, npix_x: int, npix_y: int
     x0 = -(vmin + (np.arange(nch) + 0.5) * dv) / b          # -v_k / b
     vel = d["vel"]
     tau0 = d["tau0"]
+    tau_abs = d["tau_abs"]                                   # continuum opacity, or None
     em = np.asarray(emiss, dtype=np.float64).reshape(-1, nch)
     jl = None if jline is None else np.asarray(jline, dtype=np.float64).reshape(-1)
     pix_h = fov / npix_x
@@ -93,6 +96,8 @@ def trace_maps(oracle_mod, problem, emiss, camera: int, npix_x: int, npix_y: int
             xk = x0 - vn
             H = T.voigt_lookup(xk, d["a"], lnH, H0)
             alpha = tau0[c] * H
+            if tau_abs is not None:                         # line plus continuum extinction
+                alpha = alpha + tau_abs[c]
             dtau = alpha * dl
             j = em[c].copy()
             if jl is not None:

@@ -30,10 +30,10 @@ KRL_PROFILE = {"line_centre": 0, "gaussian": 1}
 KRL_TALLY = {"scatmap": 1, "exc": 2, "J": 4, "emiss": 8}
 KRL_PREC_FP32, KRL_PREC_FP64 = 0, 1
 KRL_MAX_CAMERAS = 8
-OUT = {"spec_w": 0, "spec_n": 1, "scatmap": 2, "exc": 3, "J": 4, "emiss": 5, "stats": 6,
+OUT = {"spec_w": 0, "spec_n": 1, "scatmap": 2, "exc": 3, "J": 4, "emiss": 5, "stats": 6, "absw": 7,
        "voigt": 16, "us_x": 17, "us_lncdf": 18, "rtab": 19, "cells": 20, "eps": 21, "src_cdf": 22, "H0": 23,
        "voigt2d": 24}
-OUT_DTYPE = {0: "float64", 1: "int64", 2: "int64", 3: "float64", 4: "float64", 5: "float32", 6: "int64",
+OUT_DTYPE = {0: "float64", 1: "int64", 2: "int64", 3: "float64", 4: "float64", 5: "float32", 6: "int64", 7: "float64",
              16: "float32", 17: "float32", 18: "float32", 19: "float32", 20: "float32", 21: "float32",
              22: "float64", 23: "float32", 24: "float32"}
 
@@ -48,7 +48,7 @@ class krl_grid_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("cell_cm", C.c_double),
                 ("boundary_flags", C.c_uint32), ("opacity_kind", C.c_int), ("opacity", C.c_void_p),
                 ("T_K", C.c_double), ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p),
-                ("n_coll", C.c_void_p)]
+                ("n_coll", C.c_void_p), ("tau_abs", C.c_void_p)]
 
 
 class krl_line_desc(C.Structure):
@@ -105,7 +105,8 @@ class krl_tune(C.Structure):
 
 class krl_run_stats(C.Structure):
     _fields_ = [("emitted", C.c_uint64), ("escaped", C.c_uint64), ("destroyed", C.c_uint64),
-                ("stuck", C.c_uint64), ("scatterings", C.c_uint64), ("crossings", C.c_uint64)]
+                ("stuck", C.c_uint64), ("scatterings", C.c_uint64), ("crossings", C.c_uint64),
+                ("absorbed", C.c_uint64)]
 
 
 RECORD_DTYPE = np.dtype([("x", "<f4"), ("nscat", "<u4"), ("ncross", "<u4"), ("status", "<u2"),
@@ -267,6 +268,7 @@ class Grid:
         if problem.vel_cms is not None:
             vel = [dev(problem.vel_cms[k]) for k in range(3)]
         nco = dev(problem.n_coll)
+        tab = dev(getattr(problem, "tau_abs", None))
         d = krl_grid_desc()
         d.nx, d.ny, d.nz = nx, ny, nz
         d.cell_cm = problem.cell_cm
@@ -276,6 +278,7 @@ class Grid:
         d.T_K = problem.T_K
         d.vx, d.vy, d.vz = [v.data_ptr() if v is not None else None for v in vel]
         d.n_coll = nco.data_ptr() if nco is not None else None
+        d.tau_abs = tab.data_ptr() if tab is not None else None
         self.handle = krl_grid_create(d, stream)
         try:
             ln, src = problem.line, problem.source

@@ -25,6 +25,7 @@ struct krl_grid {
     float* opacity = nullptr;
     float* vel[3] = {nullptr, nullptr, nullptr};
     float* n_coll = nullptr;
+    float* tau_abs = nullptr;            // continuum absorption per cell width, or NULL
     bool has_vel = false;
     // line
     bool line_ok = false;
@@ -44,6 +45,7 @@ struct krl_grid {
     double* exc = nullptr;
     double* J = nullptr;
     float* emiss = nullptr;
+    double* absw = nullptr;                   // [ncell] weight absorbed by the continuum
     unsigned long long* stats = nullptr;      // cumulative [ST_N]
     // scratch: a ring of per-run slots so that runs on different streams can
     // be in flight together (each slot: work counter + ST_N run counters)
@@ -149,6 +151,7 @@ size_t tally_elems(const krl_grid* g, krl_tally_kind k, size_t* esz)
     case KRL_OUT_J: *esz = 8; return g->J ? (size_t)g->ncell * L.n_ch : 0;
     case KRL_OUT_EMISS: *esz = 4; return g->emiss ? (size_t)L.n_cam * g->ncell * L.n_ch : 0;
     case KRL_OUT_STATS: *esz = 8; return g->stats ? (size_t)ST_N : 0;
+    case KRL_OUT_ABSW: *esz = 8; return g->absw ? (size_t)g->ncell : 0;
     case KRL_OUT_VOIGT: *esz = 4; return g->tab.voigt_lnH ? (size_t)kVoigtN : 0;
     case KRL_OUT_US_X: *esz = 4; return g->tab.us_x ? (size_t)kUsNx : 0;
     case KRL_OUT_US_LNCDF: *esz = 4; return g->tab.us_lncdf ? (size_t)kUsNx * kUsNu : 0;
@@ -173,6 +176,7 @@ const void* tally_ptr(const krl_grid* g, krl_tally_kind k)
     case KRL_OUT_J: return g->J;
     case KRL_OUT_EMISS: return g->emiss;
     case KRL_OUT_STATS: return g->stats;
+    case KRL_OUT_ABSW: return g->absw;
     case KRL_OUT_VOIGT: return g->tab.voigt_lnH;
     case KRL_OUT_US_X: return g->tab.us_x;
     case KRL_OUT_US_LNCDF: return g->tab.us_lncdf;
@@ -188,7 +192,7 @@ const void* tally_ptr(const krl_grid* g, krl_tally_kind k)
 
 krl_status zero_tallies(krl_grid* g, cudaStream_t s)
 {
-    for (int k = 0; k <= (int)KRL_OUT_STATS; ++k) {
+    for (int k = 0; k <= (int)KRL_OUT_ABSW; ++k) {
         size_t esz;
         size_t n = tally_elems(g, (krl_tally_kind)k, &esz);
         if (n) KRL_CUDA(cudaMemsetAsync((void*)tally_ptr(g, (krl_tally_kind)k), 0, n * esz, s), "zero tallies");
@@ -203,7 +207,7 @@ unsigned features_of(const krl_grid* g)
     unsigned f = 0;
     if (g->has_vel) f |= F_VEL;
     if (L.tally_flags & KRL_TALLY_SCATMAP) f |= F_SCAT;
-    if ((L.tally_flags & (KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS)) || g->eps) f |= F_RICH;
+    if ((L.tally_flags & (KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS)) || g->eps || g->tau_abs) f |= F_RICH;
     return f;
 }
 
@@ -242,8 +246,8 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.spec_hi = L.spec_xmax;
     A.spec_n = L.spec_nbins;
     A.n_ch = L.n_ch;
-    A.ch_x0 = (float)(L.ch_vmin_cms / g->info.b_cms);
-    A.ch_dx = (float)(L.ch_dv_cms / g->info.b_cms);
+    A.ch_x0 = L.ch_vmin_cms / g->info.b_cms;
+    A.ch_dx = L.ch_dv_cms / g->info.b_cms;
     A.n_cam = L.n_cam;
     for (int m = 0; m < L.n_cam; ++m) {
         double th = L.cam_theta[m], ph = L.cam_phi[m];
@@ -266,6 +270,8 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.keys = round_keys(seed);
     A.max_iters = T.max_iters;
     A.refill_min = T.refill_min;
+    A.tau_abs = g->tau_abs;
+    A.absw = g->absw;
     A.ph_mode = g->line.ph_mode;
     A.voigt2d = g->voigt2d;
     A.v2_row = g->v2_row;
@@ -360,6 +366,8 @@ krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (src[k]) e = dalloc(&g->vel[k], n);
     if (e == cudaSuccess && d->n_coll) e = dalloc(&g->n_coll, n);
+    if (e == cudaSuccess && d->tau_abs) e = dalloc(&g->tau_abs, n);
+    if (e == cudaSuccess && d->tau_abs) e = dalloc(&g->absw, n);
     if (e == cudaSuccess) e = dalloc(&g->stats, ST_N);
     if (e == cudaSuccess) e = dalloc(&g->run_stats, (size_t)kSlots * ST_N);
     if (e == cudaSuccess) e = dalloc(&g->next, (size_t)kSlots);
@@ -369,7 +377,11 @@ krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (src[k]) e = cudaMemcpyAsync(g->vel[k], src[k], n * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && d->n_coll) e = cudaMemcpyAsync(g->n_coll, d->n_coll, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && d->tau_abs)
+        e = cudaMemcpyAsync(g->tau_abs, d->tau_abs, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && g->absw) e = cudaMemsetAsync(g->absw, 0, n * 8, s);
     if (e == cudaSuccess) e = validate_field(g->opacity, g->ncell, false, g->bad, s);
+    if (e == cudaSuccess && g->tau_abs) e = validate_field(g->tau_abs, g->ncell, false, g->bad, s);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (g->vel[k]) e = validate_field(g->vel[k], g->ncell, true, g->bad, s);
     if (e == cudaSuccess && g->n_coll) e = validate_field(g->n_coll, g->ncell, false, g->bad, s);
@@ -383,7 +395,7 @@ krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st
     }
     if (bad) {
         krl_grid_destroy(g);
-        return fail(KRL_ERR_NUMERIC, "grid field holds NaN/Inf or a negative opacity/density");
+        return fail(KRL_ERR_NUMERIC, "grid field holds NaN/Inf or a negative opacity/density/absorption");
     }
     *out = g;
     return KRL_OK;
@@ -397,6 +409,8 @@ krl_status krl_grid_destroy(krl_grid* g)
     dfree(g->opacity);
     for (int k = 0; k < 3; ++k) dfree(g->vel[k]);
     dfree(g->n_coll);
+    dfree(g->tau_abs);
+    dfree(g->absw);
     dfree(g->lv_gamma);
     dfree(g->lv_pops0);
     dfree(g->lv_rate);
@@ -603,6 +617,7 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
         stats->stuck = h[ST_STUCK];
         stats->scatterings = h[ST_SCAT];
         stats->crossings = h[ST_CROSS];
+        stats->absorbed = h[ST_ABSORBED];
         if (h[ST_STUCK]) return fail(KRL_ERR_BUDGET, "%llu packets exhausted max_iters", h[ST_STUCK]);
     }
     return KRL_OK;
@@ -637,6 +652,7 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
     }
     RayArgs A{};
     A.cells = g->cells;
+    A.tau_abs = g->tau_abs;
     A.nx = g->nx;
     A.ny = g->ny;
     A.nz = g->nz;
@@ -790,7 +806,7 @@ krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* 
         for (size_t m = 0; m < n; ++m) {
             const unsigned long long* c = h.data() + m * ST_N;
             stats[m] = krl_run_stats{c[ST_EMITTED], c[ST_ESCAPED], c[ST_DESTROYED], c[ST_STUCK], c[ST_SCAT],
-                                     c[ST_CROSS]};
+                                     c[ST_CROSS], c[ST_ABSORBED]};
             stuck += c[ST_STUCK];
         }
         if (stuck) return fail(KRL_ERR_BUDGET, "%llu packets exhausted max_iters", stuck);

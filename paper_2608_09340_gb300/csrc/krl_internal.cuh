@@ -51,7 +51,10 @@ enum : unsigned {
     F_RICH = 4u,      // excitation / mean intensity / emissivity / destruction
 };
 
-enum { ST_EMITTED = 0, ST_ESCAPED, ST_DESTROYED, ST_STUCK, ST_SCAT, ST_CROSS, ST_N = 8 };
+enum { ST_EMITTED = 0, ST_ESCAPED, ST_DESTROYED, ST_STUCK, ST_SCAT, ST_CROSS, ST_ABSORBED, ST_N = 8 };
+
+// A packet whose weight falls below this after continuum absorption ends.
+constexpr double kWeightCut = 1e-12;
 
 // Philox4x32-10 round keys of a launch: k[0][r] = key_lo + r 0x9E3779B9,
 // k[1][r] = key_hi + r 0xBB67AE85 (mod 2^32). Precomputed on the host and
@@ -77,6 +80,8 @@ inline RoundKeys round_keys(unsigned long long seed)
 struct TransportArgs {
     const float4* cells;      // {line-centre tau per cell width, Vx/b, Vy/b, Vz/b}
     const float* eps;         // per-cell destruction probability or nullptr
+    const float* tau_abs;     // per-cell continuum absorption per cell width or nullptr
+    double* absw;             // [ncell] absorbed weight (with tau_abs)
     int nx, ny, nz, ncell;
     unsigned periodic;        // bit d set: axis d periodic
     double a;                 // damping parameter (the FP32 walk rounds it once)
@@ -93,7 +98,7 @@ struct TransportArgs {
     double spec_lo, spec_hi;
     int spec_n;
     int n_ch;
-    float ch_x0, ch_dx;       // v_min / b, dv / b
+    double ch_x0, ch_dx;      // v_min / b, dv / b (the FP32 walk rounds them once)
     int n_cam;
     float cam[KRL_MAX_CAMERAS][3];
     unsigned rich;            // KRL_TALLY_EXC | KRL_TALLY_J | KRL_TALLY_EMISS, eps present (bit 16)
@@ -157,6 +162,7 @@ int transport_max_block(int precision, unsigned features);
 // ---------------------------------------------------------------- ray trace (raytrace.cu)
 struct RayArgs {
     const float4* cells;      // per-cell record (alpha0 dx, V/b)
+    const float* tau_abs;     // continuum absorption per cell width, or nullptr
     int nx, ny, nz;
     const float* voigt_lnH;
     const float* H0;

@@ -7,10 +7,12 @@
 // direction n (image axes e_theta, e_phi of the camera angles), centred on
 // the box. For a cell segment of length dl and channel k, with gas-frame
 // frequency x_k = -(v_k + n.V)/b,
-//   alpha_k = alpha0 H(a, x_k),  dtau = alpha_k dl,
+//   alpha_k = alpha0 H(a, x_k) + alpha_abs,  dtau = alpha_k dl,
 //   I_out = I_in e^{-dtau} + j_k dl (1 - e^{-dtau}) / dtau,
 //   j_k = j_sca,k + j_line H(a, x_k) / sqrt(pi),
-// i.e. S_k = j_k / alpha_k in Eq. imaging-formal, finite for empty cells.
+// i.e. S_k = j_k / alpha_k in Eq. imaging-formal, finite for empty cells;
+// alpha_abs is the continuum absorption (zero without one), applied here in
+// the imaging pass as the two-step scheme does (Sec. 3.2).
 //
 // GPU layout: one warp per pixel, channels across lanes, so that a cell's
 // [n_ch] emissivity row is one coalesced read and the walk is shared by the
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
             float vnh, vnl;
             dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
             const float jl = A.jline ? __ldg(A.jline + c) : 0.0f;
+            const float ta = A.tau_abs ? __ldg(A.tau_abs + c) : 0.0f;
             const float* jrow = A.emiss + (size_t)c * A.n_ch;
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
                 if (k < A.n_ch) {
                     const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
                     const float H = voigt_rt(xk, sv, eI, eF, a, H0);
-                    const float dtau = rec.x * H * s;
+                    const float dtau = fmaf(rec.x, H, ta) * s;
                     float j = __ldg(jrow + k);
                     if (A.jline) j = fmaf(jl * 0.56418958354775628f, H, j);
                     const float T = __expf(-tau[q]);

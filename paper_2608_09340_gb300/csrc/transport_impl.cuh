@@ -295,7 +295,9 @@ struct Pkt {
     uint32_t nscat, ncross, cell0;
     unsigned long long id;
     uint32_t vis_scat;     // scatterings in this cell visit
-    R vis_exc;             // sum ds H over this cell visit
+    R vis_exc;             // sum w ds H over this cell visit
+    R wgt;                 // packet weight (continuum absorption; 1 otherwise)
+    R vis_abs;             // weight absorbed by the continuum over this visit
     bool prev_scat;        // last event was a scattering (draw the next one early)
 };
 
@@ -353,7 +355,7 @@ __device__ __forceinline__ void iso_dir(R umu, R uphi, R& nx, R& ny, R& nz)
     nz = mu;
 }
 
-__device__ __forceinline__ void spectrum_add(const TransportArgs& A, double x)
+__device__ __forceinline__ void spectrum_add(const TransportArgs& A, double x, double w)
 {
     int b;
     if (x < A.spec_lo) b = 0;
@@ -362,7 +364,7 @@ __device__ __forceinline__ void spectrum_add(const TransportArgs& A, double x)
         b = 1 + (int)floor((x - A.spec_lo) / (A.spec_hi - A.spec_lo) * A.spec_n);
         if (b > A.spec_n) b = A.spec_n;
     }
-    atomicAdd(A.spec_w + b, 1.0);
+    atomicAdd(A.spec_w + b, w);
     atomicAdd(A.spec_c + b, 1ull);
 }
 
@@ -464,6 +466,8 @@ __device__ bool emit(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p)
     p.ncross = 0;
     p.vis_scat = 0;
     p.vis_exc = (R)0;
+    p.wgt = (R)1;
+    p.vis_abs = (R)0;
     p.prev_scat = true;
     if (!inside) {
         p.x = xcom;
@@ -488,14 +492,14 @@ __device__ bool emit(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p)
 // and the camera-directed emissivity (Eq. scat-line with the trilinear
 // R_IIA table, Eq. riia-table, or Eq. riia-inf for |x_in| >= 120).
 template <typename R, unsigned F>
-__device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xcom, R H)
+__device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xcom, R H, R w)
 {
     if ((A.rich & KRL_TALLY_J) && A.n_ch > 0) {
         R q = Ops<R>::dv(-xcom - (R)A.ch_x0, (R)A.ch_dx);
-        if (q >= (R)0 && q < (R)A.n_ch) atomicAdd(A.J + (size_t)p.c * A.n_ch + (int)q, (double)ds);
+        if (q >= (R)0 && q < (R)A.n_ch) atomicAdd(A.J + (size_t)p.c * A.n_ch + (int)q, (double)(w * ds));
     }
     if (!(A.rich & KRL_TALLY_EMISS) || A.n_ch <= 0) return;
-    const R base = ds * (R)p.rec.x * H * (R)0.079577471545947668;   // 1 / 4 pi
+    const R base = w * ds * (R)p.rec.x * H * (R)0.079577471545947668;   // 1 / 4 pi
     const R axc = fabs(xcom);
     const R sgn = xcom < (R)0 ? (R)-1 : (R)1;    // R(D; -x, g) = R(-D; x, g)
     for (int m = 0; m < A.n_cam; ++m) {
@@ -560,8 +564,10 @@ __device__ __forceinline__ void flush_visit(const TransportArgs& A, Pkt<R>& p)
 {
     if ((F & F_SCAT) && p.vis_scat && A.scat) atomicAdd(A.scat + p.c, (unsigned long long)p.vis_scat);
     if ((F & F_RICH) && (A.rich & KRL_TALLY_EXC) && p.vis_exc != (R)0) atomicAdd(A.exc + p.c, (double)p.vis_exc);
+    if ((F & F_RICH) && A.tau_abs && p.vis_abs != (R)0) atomicAdd(A.absw + p.c, (double)p.vis_abs);
     p.vis_scat = 0;
     p.vis_exc = (R)0;
+    p.vis_abs = (R)0;
 }
 
 template <typename T>
@@ -580,7 +586,7 @@ constexpr int max_block() { return (sizeof(R) == 4 && !(F & F_RICH)) ? 512 : 256
 
 // Per-lane event counters (summed over the CTA at the end of a model).
 struct LaneStats {
-    unsigned long long emit, esc, des, stuck, scat, cross;
+    unsigned long long emit, esc, des, stuck, scat, cross, absorbed;
 };
 
 // ---------------------------------------------------------------- tail compaction
@@ -596,12 +602,13 @@ constexpr size_t kStashOff = kCtlOff + (size_t)kCtlInts * sizeof(int);
 constexpr int kTailRound = 32;
 
 // Words per stashed packet: cell (c, cx, cy, cz), nscat, ncross, cell0, id
-// (2 words), and px, py, pz, nx, ny, nz, x, tau in R.
-template <typename R>
-constexpr int stash_words() { return 9 + 8 * (int)(sizeof(R) / 4); }
+// (2 words), and px, py, pz, nx, ny, nz, x, tau (and the weight in the rich
+// walk) in R.
+template <typename R, unsigned F>
+constexpr int stash_words() { return 9 + ((F & F_RICH) ? 9 : 8) * (int)(sizeof(R) / 4); }
 
 template <typename R, unsigned F>
-constexpr size_t smem_bytes(int block) { return kStashOff + (size_t)stash_words<R>() * 4u * (size_t)block; }
+constexpr size_t smem_bytes(int block) { return kStashOff + (size_t)stash_words<R, F>() * 4u * (size_t)block; }
 
 template <typename R>
 __device__ __forceinline__ void put_r(uint32_t* w, int& f, int n, int slot, R v)
@@ -631,7 +638,7 @@ __device__ __forceinline__ R get_r(const uint32_t* w, int& f, int n, int slot)
 // derived fields (1/n, the cell record) are recomputed from the stored ones
 // by the same functions, so a restored packet continues bit for bit as it
 // would have in its old lane.
-template <typename R>
+template <typename R, unsigned F>
 __device__ __forceinline__ void stash_put(uint32_t* w, int n, int slot, const Pkt<R>& p)
 {
     int f = 0;
@@ -652,9 +659,10 @@ __device__ __forceinline__ void stash_put(uint32_t* w, int n, int slot, const Pk
     put_r<R>(w, f, n, slot, p.nz);
     put_r<R>(w, f, n, slot, p.x);
     put_r<R>(w, f, n, slot, p.tau);
+    if (F & F_RICH) put_r<R>(w, f, n, slot, p.wgt);
 }
 
-template <typename R>
+template <typename R, unsigned F>
 __device__ __forceinline__ void stash_get(const TransportArgs& A, const uint32_t* w, int n, int slot, Pkt<R>& p)
 {
     int f = 0;
@@ -677,13 +685,28 @@ __device__ __forceinline__ void stash_get(const TransportArgs& A, const uint32_t
     set_dir(p, nx, ny, nz);
     p.x = get_r<R>(w, f, n, slot);
     p.tau = get_r<R>(w, f, n, slot);
+    p.wgt = (F & F_RICH) ? get_r<R>(w, f, n, slot) : (R)1;
     p.rec = __ldg(A.cells + p.c);
     p.vis_scat = 0;
     p.vis_exc = (R)0;
+    p.vis_abs = (R)0;
     p.prev_scat = true;
 }
 
 // ---------------------------------------------------------------- one event
+
+// Continuum absorption over a segment of optical depth dt (Eq. scat-line):
+// ab = 1 - exp(-dt) is the absorbed fraction of the weight, and the
+// returned factor (1 - exp(-dt))/dt the segment's mean weight per unit
+// starting weight (its series below dt = 1e-4).
+template <typename R>
+__device__ __forceinline__ R seg_factor(R dt, R& ab)
+{
+    if constexpr (sizeof(R) == 4) ab = -expm1f(-dt);
+    else ab = -expm1(-dt);
+    if (dt < (R)1e-4) return (R)1 - dt * ((R)0.5 - dt * ((R)(1.0 / 6.0) - dt * (R)(1.0 / 24.0)));
+    return ab / dt;
+}
 
 // Advances an active packet by one event in its current cell (a scattering
 // inside the cell or a crossing of the nearest face). Returns false when the
@@ -732,8 +755,24 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
     p.py = O::step01(p.py, ds, p.ny);
     p.pz = O::step01(p.pz, ds, p.nz);
     if (F & F_RICH) {
-        if (A.rich & KRL_TALLY_EXC) p.vis_exc += ds * H;
-        if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H);
+        // segment tallies at the mean weight along the segment; the weight
+        // then decays by the continuum's absorption over it
+        R wseg = p.wgt, ab = (R)0;
+        if (A.tau_abs) wseg = p.wgt * seg_factor<R>((R)__ldg(A.tau_abs + p.c) * ds, ab);
+        if (A.rich & KRL_TALLY_EXC) p.vis_exc += wseg * ds * H;
+        if (A.rich & (KRL_TALLY_J | KRL_TALLY_EMISS)) rich_segment<R, F>(A, p, ds, xcom, H, wseg);
+        if (A.tau_abs) {
+            p.vis_abs += p.wgt * ab;
+            p.wgt = p.wgt * ((R)1 - ab);
+            if (p.wgt < (R)kWeightCut) {
+                flush_visit<R, F>(A, p);
+                ++st.absorbed;
+                st.scat += p.nscat;
+                st.cross += p.ncross;
+                write_record(A, p, 4);
+                return false;
+            }
+        }
     }
     p.prev_scat = scat;
     if (scat) {
@@ -795,7 +834,7 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
     else p.pz = pnew;
     if (nc < 0 || nc >= dim) {
         if (!((A.periodic >> axis) & 1u)) {
-            spectrum_add(A, (double)p.x);
+            spectrum_add(A, (double)p.x, (double)p.wgt);
             ++st.esc;
             st.scat += p.nscat;
             st.cross += p.ncross;
@@ -860,7 +899,7 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
     const int nwarps = (int)(blockDim.x >> 5);
     Pkt<R> p;
     bool active = false;
-    LaneStats st = {0, 0, 0, 0, 0, 0};
+    LaneStats st = {0, 0, 0, 0, 0, 0, 0};
 
     // Both phases run in one loop so that the event code is inlined once.
     const int n = (int)blockDim.x;
@@ -888,7 +927,7 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
                         if (emit<R, F>(A, K, p)) {
                             active = true;
                         } else {
-                            spectrum_add(A, (double)p.x);
+                            spectrum_add(A, (double)p.x, 1.0);
                             ++st.esc;
                             write_record(A, p, 1);
                         }
@@ -916,13 +955,13 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
             if (busy > (total + 31) / 32) {   // CTA-uniform
                 if (active) {
                     flush_visit<R, F>(A, p);
-                    stash_put<R>(stash, n, before + __popc(m & ((1u << lane) - 1u)), p);
+                    stash_put<R, F>(stash, n, before + __popc(m & ((1u << lane) - 1u)), p);
                 }
                 __syncthreads();
                 // the stash is next written after a later round's count
                 // barrier, which every thread reaches only after this read
                 active = (int)threadIdx.x < total;
-                if (active) stash_get<R>(A, stash, n, (int)threadIdx.x, p);
+                if (active) stash_get<R, F>(A, stash, n, (int)threadIdx.x, p);
             }
             ++round;
             it = 0;
@@ -931,11 +970,12 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
         if (active) active = advance<R, F, PH>(A, K, p, sv, sx, sc, sg, a, H0, st);
     }
 
-    const unsigned long long tot[6] = {warp_sum(st.emit), warp_sum(st.esc),  warp_sum(st.des),
-                                       warp_sum(st.stuck), warp_sum(st.scat), warp_sum(st.cross)};
+    const unsigned long long tot[7] = {warp_sum(st.emit),  warp_sum(st.esc),  warp_sum(st.des),
+                                       warp_sum(st.stuck), warp_sum(st.scat), warp_sum(st.cross),
+                                       warp_sum(st.absorbed)};
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
+        for (int k = 0; k < 7; ++k)
             if (tot[k]) atomicAdd(A.stats + k, tot[k]);
     }
 }

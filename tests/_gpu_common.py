@@ -24,7 +24,7 @@ def gpu_run(krl, problem, precision, n=None, first=0, seed=None, records=True, t
         if records:
             out["records"] = krl.records_to_numpy(rec)
         if tallies:
-            for name in ("spec_w", "spec_n", "scatmap", "exc", "J", "emiss", "stats"):
+            for name in ("spec_w", "spec_n", "scatmap", "exc", "J", "emiss", "stats", "absw"):
                 t = g.tally(name)
                 out["stats_tally" if name == "stats" else name] = None if t is None else t.cpu().numpy()
         return out
