@@ -40,8 +40,9 @@ UNIT = "scatterings/s"
 OPS_PER_SCAT = 330
 OPS_PER_CROSS = 50
 FP32_LANES_PER_SM = 128
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "transport_sphere64_tau3e4.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_2608_09340_gb300", "csrc", "transport.cu")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "transport_sphere64_tau1e4.txt")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2608_09340_gb300", "csrc", f)
+              for f in ("transport_impl.cuh", "transport.cu")]
 
 
 def parse():
@@ -136,7 +137,7 @@ def traffic_from_profile():
     taken on the current kernel source (else None)."""
     try:
         txt = open(PROFILE_SUMMARY).read()
-        src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        src_hash = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRC)).hexdigest()[:16]
         vals = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith(" "))
         if vals.get("kernel_source_sha256_16", "").strip() != src_hash:
             return None

@@ -152,7 +152,8 @@ typedef struct {
           sampler read from global memory; needs 1e-6 <= a <= 1;
        3: the core-wing approximation (1 - w) exp(-x^2) + w a / (sqrt(pi)(x^2 +
           a^2)), w = [1 + tanh(2|x| - 2 u0)] / 2, u0 the outer crossing point of
-          the two terms; a demonstration, not for production; needs a < 0.8.
+          the two terms; it shows what an inconsistent profile costs and is unsuited
+          to production runs; needs a < 0.8.
        Modes 1 and 3 run krl_run_packets only (KRL_ERR_ARG from krl_batch_run
        and krl_raytrace_channels, which use the mode 2 slice).                 */
     int ph_mode;
