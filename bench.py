@@ -182,10 +182,14 @@ def bench_raytrace(args, dev):
     finally:
         g.close()
     rays = RT_CAMERAS * RT_PIXELS * RT_PIXELS
+    cube = RT_CAMERAS * RT_GRID ** 3 * RT_CHANNELS * 4
     return {"workload": f"envelope {RT_GRID}^3, {RT_CHANNELS} ch, {RT_PIXELS}^2 px, {RT_CAMERAS} inclinations",
             "rays_per_s": rays / ms * 1e3, "channel_rays_per_s": rays * RT_CHANNELS / ms * 1e3,
-            "ms_per_pass": ms, "passes": reps, "gpu_launches_per_pass": RT_CAMERAS,
-            "emissivity_bytes": RT_CAMERAS * RT_GRID ** 3 * RT_CHANNELS * 4}
+            "ms_per_pass": ms, "passes": reps,
+            "gpu_launches_per_pass": 2 * RT_CAMERAS,      # per camera: profile cube, then the trace
+            "emissivity_bytes": cube,
+            "min_hbm_gbs": cube / ms / 1e6,               # the emissivity cube read once per pass
+            "l2": "inputs larger than L2 (emissivity 12.9 GB per pass)"}
 
 
 BATCH_MODELS = 64

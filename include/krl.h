@@ -373,10 +373,15 @@ typedef struct {
  * camera direction n, image axes (e_theta, e_phi), centred on the box, no
  * incoming intensity; per cell segment dl and channel k (the line's
  * v_k = v_min + (k + 1/2) dv, 1 <= n_ch <= 128) with x_k = -(v_k + n.V)/b:
- * I <- I e^{-dtau} + j_k dl (1 - e^{-dtau})/dtau, dtau = alpha0 H(a, x_k) dl,
+ * I <- I e^{-dtau} + j_k dl (1 - e^{-dtau})/dtau, dtau = (alpha0 H(a, x_k) +
+ * tau_abs) dl (tau_abs: the grid's continuum, zero without one),
  * j_k = emiss_k + jline H(a, x_k)/sqrt(pi). maps: device float32
  * [n_ch][npix_y][npix_x], written (raw units: emissivity x cell widths).
  * All faces are open for the rays. Enqueued on `s`; does not synchronise.
+ * H(a, x_k) depends on the cell and the channel only, so it is tabulated
+ * once per call in a stream-ordered scratch of ncell x n_ch floats
+ * (cudaMallocAsync on `s`, freed on `s` after the trace); when that memory
+ * is not available the trace evaluates H per segment, with the same result.
  */
 KRL_API krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float* maps, krl_stream s);
 

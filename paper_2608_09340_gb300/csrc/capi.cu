@@ -680,7 +680,22 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
     A.npix_x = d->npix_x;
     A.npix_y = d->npix_y;
     A.maps = maps;
-    KRL_CUDA(launch_raytrace(A, (cudaStream_t)st), "ray trace launch");
+    // Per-camera profile cube, stream-ordered scratch (so calls on different
+    // streams never share it). Without the memory the trace evaluates the
+    // profile per segment instead, with the same result.
+    cudaStream_t s = (cudaStream_t)st;
+    const size_t hbytes = (size_t)g->ncell * (size_t)L.n_ch * sizeof(float);
+    A.hcube = nullptr;
+    if (cudaMallocAsync((void**)&A.hcube, hbytes, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        A.hcube = nullptr;
+    }
+    cudaError_t e = launch_raytrace(A, g->num_sms, s);
+    if (A.hcube) {
+        cudaError_t ef = cudaFreeAsync(A.hcube, s);
+        if (e == cudaSuccess) e = ef;
+    }
+    KRL_CUDA(e, "ray trace launch");
     return KRL_OK;
 }
 

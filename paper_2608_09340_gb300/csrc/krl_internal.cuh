@@ -169,6 +169,8 @@ struct RayArgs {
     float a;
     const float* emiss;       // [ncell][n_ch] camera-directed scattering emissivity
     const float* jline;       // [ncell] frequency-integrated line emission, or nullptr
+    float* hcube;             // [ncell][n_ch] scratch for the per-camera profile, or nullptr
+                              // (then the trace evaluates the profile per segment)
     int n_ch;
     double ch_x0, ch_dx;      // v_min / b, dv / b
     double n[3], u[3], v[3];  // camera direction and image axes
@@ -177,7 +179,7 @@ struct RayArgs {
     int npix_x, npix_y;
     float* maps;              // [n_ch][npix_y][npix_x]
 };
-cudaError_t launch_raytrace(const RayArgs& A, cudaStream_t s);
+cudaError_t launch_raytrace(const RayArgs& A, int sm_count, cudaStream_t s);
 
 // ---------------------------------------------------------------- statistical equilibrium (levels.cu)
 constexpr int kMaxLevels = KRL_MAX_LEVELS;

@@ -103,7 +103,62 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v)
     sum = t;
 }
 
+// Per-camera profile cube: for every (cell, channel), H(a, x_k) with
+// x_k = -(v_k + n.V)/b. Along one camera direction x_k depends on the cell
+// and the channel only, not on the ray, so the trace reads it from here
+// instead of evaluating the profile for each of the ~16 rays that cross a
+// cell. The arithmetic is the trace's own (float-pair n.V, exponent-split
+// table index). One warp per cell, channels across lanes.
 template <int CPL>
+__global__ void __launch_bounds__(256) k_rt_profile(const RayArgs A, float* hc)
+{
+    __shared__ float sv[kVoigtN];
+    __shared__ int eI[kRtEn];
+    __shared__ float eF[kRtEn];
+    for (int i = threadIdx.x; i < kVoigtN; i += blockDim.x) sv[i] = A.voigt_lnH[i];
+    if (threadIdx.x < kRtEn) {
+        const double t = (double)((kVoigtN - 1) / (kVoigtL1 - kVoigtL0)) *
+                         (((int)threadIdx.x + kRtEmin) * 0.30102999566398119521 - kVoigtL0);
+        const double it = floor(t);
+        eI[threadIdx.x] = (int)it;
+        eF[threadIdx.x] = (float)(t - it);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long ncell = (long long)A.nx * A.ny * A.nz;
+    float nh[3], nl[3];
+    for (int d = 0; d < 3; ++d) {
+        nh[d] = (float)A.n[d];
+        nl[d] = (float)(A.n[d] - (double)nh[d]);
+    }
+    float xbh[CPL], xbl[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const double xb = -(A.ch_x0 + ((double)(lane + 32 * q) + 0.5) * A.ch_dx);
+        xbh[q] = (float)xb;
+        xbl[q] = (float)(xb - (double)xbh[q]);
+    }
+    const float a = A.a;
+    const float H0 = __ldg(A.H0);
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncell; c += nwarps) {
+        const float4 rec = __ldg(A.cells + c);
+        float vnh, vnl;
+        dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const int k = lane + 32 * q;
+            if (k < A.n_ch) {
+                const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
+                hc[(size_t)c * A.n_ch + k] = voigt_rt(xk, sv, eI, eF, a, H0);
+            }
+        }
+    }
+}
+
+// PRE: read H(a, x_k) from the per-camera cube A.hcube (k_rt_profile)
+// instead of evaluating it per segment.
+template <int CPL, bool PRE>
 __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
 {
     __shared__ float sv[kVoigtN];
@@ -190,17 +245,23 @@ __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
             const int c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
             const float4 rec = __ldg(A.cells + c);
             // n . V/b (|V/b| reaches tens) as a float pair
-            float vnh, vnl;
-            dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
+            float vnh = 0.0f, vnl = 0.0f;
+            if (!PRE) dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
             const float jl = A.jline ? __ldg(A.jline + c) : 0.0f;
             const float ta = A.tau_abs ? __ldg(A.tau_abs + c) : 0.0f;
             const float* jrow = A.emiss + (size_t)c * A.n_ch;
+            const float* hrow = PRE ? A.hcube + (size_t)c * A.n_ch : nullptr;
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
                 const int k = lane + 32 * q;
                 if (k < A.n_ch) {
-                    const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
-                    const float H = voigt_rt(xk, sv, eI, eF, a, H0);
+                    float H;
+                    if (PRE) {
+                        H = __ldg(hrow + k);
+                    } else {
+                        const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
+                        H = voigt_rt(xk, sv, eI, eF, a, H0);
+                    }
                     const float dtau = fmaf(rec.x, H, ta) * s;
                     float j = __ldg(jrow + k);
                     if (A.jline) j = fmaf(jl * 0.56418958354775628f, H, j);
@@ -225,16 +286,27 @@ __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
 
 }  // namespace
 
-cudaError_t launch_raytrace(const RayArgs& A, cudaStream_t s)
+template <int CPL>
+cudaError_t launch_cpl(const RayArgs& A, long long blocks, int sm_count, cudaStream_t s)
+{
+    if (A.hcube) {
+        k_rt_profile<CPL><<<sm_count * 8, 256, 0, s>>>(A, A.hcube);
+        k_raytrace<CPL, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+    } else {
+        k_raytrace<CPL, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raytrace(const RayArgs& A, int sm_count, cudaStream_t s)
 {
     const long long npix = (long long)A.npix_x * A.npix_y;
     const long long blocks = (npix * 32 + 255) / 256;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (A.n_ch <= 32) k_raytrace<1><<<(unsigned)blocks, 256, 0, s>>>(A);
-    else if (A.n_ch <= 64) k_raytrace<2><<<(unsigned)blocks, 256, 0, s>>>(A);
-    else if (A.n_ch <= 128) k_raytrace<4><<<(unsigned)blocks, 256, 0, s>>>(A);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    if (A.n_ch <= 32) return launch_cpl<1>(A, blocks, sm_count, s);
+    if (A.n_ch <= 64) return launch_cpl<2>(A, blocks, sm_count, s);
+    if (A.n_ch <= 128) return launch_cpl<4>(A, blocks, sm_count, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace krl
