@@ -73,3 +73,26 @@ def chi2_two_sample(c1, c2, min_count=10):
     stat = np.sum((k1 * m1 - k2 * m2) ** 2 / (m1 + m2))
     dof = len(m1) - 1
     return stat, dof, chi2.sf(stat, dof) if dof > 0 else 1.0
+
+
+def x_peak(spec, lo, hi, guess):
+    """Peak of an escaped spectrum folded to |x|: the histogram (bins of
+    [lo, hi), symmetric about 0) smoothed with a Gaussian of width 0.1 guess,
+    then a parabola through the largest smoothed bin and its neighbours."""
+    c = np.asarray(spec, dtype=np.float64)
+    n = c.size
+    edges = np.linspace(lo, hi, n + 1)
+    xc = 0.5 * (edges[1:] + edges[:-1])
+    dx = edges[1] - edges[0]
+    pos = xc > 0
+    folded = c[pos] + c[~pos][::-1]
+    xs = xc[pos]
+    sig = 0.1 * guess / dx
+    k = np.arange(-int(4 * sig) - 1, int(4 * sig) + 2)
+    ker = np.exp(-0.5 * (k / sig) ** 2)
+    sm = np.convolve(folded, ker / ker.sum(), mode="same")
+    i = int(np.argmax(sm[1:-1])) + 1
+    y0, y1, y2 = sm[i - 1], sm[i], sm[i + 1]
+    den = y0 - 2 * y1 + y2
+    off = 0.5 * (y0 - y2) / den if den != 0 else 0.0
+    return xs[i] + off * dx

@@ -13,7 +13,7 @@ import pytest
 import oracle
 import workloads as W
 from oracle import tables as OT
-from _gpu_common import agreement, chi2_two_sample, gpu_run, need_gpu, rel_l1
+from _gpu_common import agreement, chi2_two_sample, gpu_run, need_gpu, rel_l1, x_peak
 
 pytestmark = pytest.mark.gpu
 
@@ -90,29 +90,6 @@ def test_fp32_walk_against_oracle(mode):
     assert chi2_two_sample(g, r)[2] > 0.01
 
 
-def _x_peak(spec, lo, hi, guess):
-    """Peak of the escaped spectrum folded to |x|: the histogram smoothed
-    with a Gaussian of width 0.1 guess, then a parabola through the
-    largest smoothed bin and its neighbours."""
-    c = np.asarray(spec, dtype=np.float64)
-    n = c.size
-    edges = np.linspace(lo, hi, n + 1)
-    xc = 0.5 * (edges[1:] + edges[:-1])
-    dx = edges[1] - edges[0]
-    pos = xc > 0
-    folded = c[pos] + c[~pos][::-1]
-    xs = xc[pos]
-    sig = 0.1 * guess / dx
-    k = np.arange(-int(4 * sig) - 1, int(4 * sig) + 2)
-    ker = np.exp(-0.5 * (k / sig) ** 2)
-    sm = np.convolve(folded, ker / ker.sum(), mode="same")
-    i = int(np.argmax(sm[1:-1])) + 1
-    y0, y1, y2 = sm[i - 1], sm[i], sm[i + 1]
-    den = y0 - 2 * y1 + y2
-    off = 0.5 * (y0 - y2) / den if den != 0 else 0.0
-    return xs[i] + off * dx
-
-
 def test_neufeld_sweep_all_modes():
     """Sec. 3.1's sweep through all three modes. The exact modes follow
     x_peak = 0.881 (a tau_m)^{1/3} within a few per cent where a tau_m is
@@ -128,7 +105,7 @@ def test_neufeld_sweep_all_modes():
             out = gpu_run(krl, p, krl.KRL_PREC_FP32, records=False, tallies=True)
             s = out["stats"]
             assert s.emitted == 100_000 == s.escaped
-            res[(tau_m, m)] = _x_peak(out["spec_n"][1:-1], -40.0, 40.0, pred) / pred
+            res[(tau_m, m)] = x_peak(out["spec_n"][1:-1], -40.0, 40.0, pred) / pred
     print("x_peak / 0.881 (a tau_m)^(1/3):",
           {f"{t:g}": [round(res[(t, m)], 4) for m in (1, 2, 3)] for t in taus})
     for t in taus:
