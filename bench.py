@@ -295,7 +295,7 @@ def cpu_baseline(p):
     """Oracle on a bounded sample (about 10 s of host work) at N = 1, rank 0."""
     import oracle
     cores = os.cpu_count() or 1
-    n = 24 * cores                  # about 10 s at the oracle's ~40 packets/s on 16 cores
+    n = 40 * cores                  # about 12 s at the oracle's ~50 packets/s on 16 cores
     oracle.line_tables(float(p.line.a_fixed), False)
     t0 = time.perf_counter()
     r = oracle.run(p, n=n, first=JOB_PACKETS - n, nthreads=cores)
