@@ -194,7 +194,8 @@ typedef struct {
     int ctas_per_sm;            /* resident CTAs per SM of the persistent grid      */
     int refill_min;             /* a warp takes new packets once at least this many
                                    of its lanes are idle (1..32)                    */
-    uint64_t max_iters;         /* per-packet cap on walk iterations (budget)       */
+    uint64_t max_iters;         /* per-packet cap on walk iterations (budget); values
+                                   above 2^32 - 1 act as 2^32 - 1                   */
 } krl_tune;
 
 /* One record per packet of a run (optional output). */

@@ -269,6 +269,7 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.k1 = (unsigned)(seed >> 32);
     A.keys = round_keys(seed);
     A.max_iters = T.max_iters;
+    A.max_iters32 = T.max_iters > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned)T.max_iters;
     A.refill_min = T.refill_min;
     A.tau_abs = g->tau_abs;
     A.absw = g->absw;

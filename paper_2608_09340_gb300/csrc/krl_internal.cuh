@@ -115,6 +115,7 @@ struct TransportArgs {
     unsigned k0, k1;
     RoundKeys keys;           // round keys of (k0, k1)
     unsigned long long max_iters;
+    unsigned max_iters32;     // min(max_iters, 2^32 - 1): the per-event check in 32 bits
     int refill_min;
     // line-profile mode (krl_line_desc.ph_mode: 2, or 1 / 3 below)
     int ph_mode;

@@ -148,7 +148,13 @@ __device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
     const R l0 = (R)sv[i], l1 = (R)sv[i + 1];
     const R tab = O::ex(((R)1 - f) * l0 + f * l1);
     const R ax2 = ax * ax;
-    const R wing = O::dv(a, (R)1.7724538509055160 * ax2) * ((R)1 + O::dv((R)1.5, ax2));
+    R wing;
+    if constexpr (sizeof(R) == 4) {
+        const float r = Ops<float>::rcp(ax2);                     // one reciprocal: a r (1 + 3r/2) / sqrt(pi)
+        wing = (a * 0.56418958354775628f) * r * fmaf(1.5f, r, 1.0f);
+    } else {
+        wing = a / ((R)1.7724538509055160 * ax2) * ((R)1 + (R)1.5 / ax2);
+    }
     return ax < (R)1e-4 ? H0 : (ax > (R)1e3 ? wing : tab);
 }
 
@@ -215,19 +221,17 @@ __device__ __forceinline__ int us_row2(R ax, const float* sx, R& x0, R& x1)
     const int ilog = 18 + (int)((R)21 * Ops<R>::ln(ax * (R)0.125) * (R)0.27588297880498553);  // 1/ln(37.5)
     int i = ax < (R)8 ? ilin : ilog;
     i = i < 0 ? 0 : (i > kUsNx - 2 ? kUsNx - 2 : i);
-    x0 = (R)sx[i];
-    x1 = (R)sx[i + 1];
-    while (i > 0 && x0 > ax) {
-        --i;
-        x1 = x0;
-        x0 = (R)sx[i];
-    }
-    while (i < kUsNx - 2 && x1 <= ax) {
-        ++i;
-        x0 = x1;
-        x1 = (R)sx[i + 1];
-    }
-    return i;
+    // The guess is off by at most one row (rounding of ax 2.25 next to a node,
+    // or the log's error next to a node): the four nodes around it are read
+    // together and the bracket is selected without a branch.
+    const R g0 = (R)sx[i], g1 = (R)sx[i + 1];
+    const R gm = (R)sx[i > 0 ? i - 1 : 0];
+    const R gp = (R)sx[i < kUsNx - 2 ? i + 2 : kUsNx - 1];
+    const bool dn = i > 0 && g0 > ax;
+    const bool up = i < kUsNx - 2 && g1 <= ax;
+    x0 = dn ? gm : (up ? g1 : g0);
+    x1 = dn ? g0 : (up ? gp : g1);
+    return i - (dn ? 1 : 0) + (up ? 1 : 0);
 }
 
 // u_par for incoming gas-frame frequency x (|x| <= 300), given L = ln(xi)
@@ -717,7 +721,7 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
                                         const float* sc, const unsigned char* sg, R a, R H0, LaneStats& st)
 {
     using O = Ops<R>;
-    if ((unsigned long long)p.nscat + p.ncross >= A.max_iters) {
+    if (p.nscat + p.ncross >= A.max_iters32) {
         flush_visit<R, F>(A, p);
         ++st.stuck;
         st.scat += p.nscat;
