@@ -372,6 +372,12 @@ def main():
         step_id += 1
     for st_ in streams:
         stream.wait_stream(st_)
+    exchange_bytes = 0
+    if world > 1:
+        # the job's one exchange: every rank ends with the whole job's tallies
+        tallies = [g.tally("spec_n"), g.tally("spec_w"), g.tally("scatmap")]
+        shard.reduce_tallies(tallies)
+        exchange_bytes = sum(t.numel() * t.element_size() for t in tallies)
     t_end.record(stream)
     barrier()
     wall = time.perf_counter() - t_wall
@@ -453,7 +459,8 @@ def main():
                        "job_packets": JOB_PACKETS, "scatterings_per_packet": scat_all / max(pk_all, 1),
                        "l2": "flushed before every timed step (256 MiB write)",
                        "steps_issue": f"{nstr} streams, round robin" if nstr > 1 else "one stream",
-                       "parallelism": f"packet-id shards x{world}"},
+                       "parallelism": f"packet-id shards x{world}",
+                       "exchange": f"tally all-reduce, {exchange_bytes} bytes per rank" if world > 1 else "none"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "raytrace": rt, "batch": bt,
             "gpu_launches": 2 * args.steps, "wall_s_timed": wall,
         }

@@ -35,3 +35,13 @@ def sum_over_ranks(tensor):
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         dist.all_reduce(tensor, op=dist.ReduceOp.SUM)
     return tensor
+
+
+def reduce_tallies(tensors):
+    """The job's one exchange: sum each rank's tallies (escaped spectrum,
+    scattering map, ...) in place, so that every rank holds the tallies of
+    the whole job. Integer tallies sum exactly; FP64 ones up to rounding."""
+    for t in tensors:
+        if t is not None:
+            sum_over_ranks(t)
+    return tensors
