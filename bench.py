@@ -300,9 +300,14 @@ def cpu_baseline(p):
     t0 = time.perf_counter()
     r = oracle.run(p, n=n, first=JOB_PACKETS - n, nthreads=cores)
     dt = time.perf_counter() - t0
+    # one core, on 4 packets of the same sample (~1 s)
+    t1 = time.perf_counter()
+    r1 = oracle.run(p, n=4, first=JOB_PACKETS - n, nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": float(r["stats"][4]) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": float(r1["stats"][4]) / dt1,
             "sample": f"{n} packets (ids {JOB_PACKETS - n}..{JOB_PACKETS - 1}) of the same static sphere, "
-                      f"{int(r['stats'][4])} scatterings in {dt:.1f} s, FP64"}
+                      f"{int(r['stats'][4])} scatterings in {dt:.1f} s, FP64; single core: the first 4 of them"}
 
 
 def main():
