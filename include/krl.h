@@ -336,9 +336,12 @@ KRL_API krl_status krl_batch_destroy(krl_batch* b);
 /*
  * Run packets[m] packets with ids [first_ids[m], first_ids[m] + packets[m])
  * (first_ids may be NULL: all 0) of every model m under one key `seed`, in
- * ONE persistent launch: each CTA takes the lowest-numbered model that still
- * has packet ids, stages that model's tables, runs its warps on it until its
- * ids run out, and moves on, so the models' tails overlap. Each packet's
+ * ONE persistent launch: the models are queued heaviest first (descending
+ * packets[m], ties by index), and each CTA takes the first queued model
+ * that still has packet ids, stages that model's tables, runs its warps on
+ * it until its ids run out, and moves on, so the models' tails overlap and
+ * the longest packets start early. CTAs are at most 256 threads
+ * (tune->block; KRL_ERR_ARG above). Each packet's
  * random stream, and therefore every tally, is exactly what krl_run_packets
  * on that grid with the same (seed, ids) gives. Tallies accumulate into each
  * grid. stats (host [n_models] or NULL): per-model counters; when given the

@@ -16,6 +16,13 @@ DEFAULT_SPACE = {
     "ctas_per_sm": (0, 1),          # 0: as many as fit
 }
 
+# The batched launch runs CTAs of at most 256 threads.
+BATCH_SPACE = {
+    "block": (128, 256),
+    "refill_min": (1, 4, 16),
+    "ctas_per_sm": (0, 1),
+}
+
 PILOT_FIRST_ID = 1 << 48            # pilot packets use ids far from any real run
 
 
@@ -40,7 +47,7 @@ def _time(fn):
 def tune_batch(batch, packets, fraction: float = 0.2, space=None, seed: int = 12345):
     """Best {block, refill_min, ctas_per_sm} for `batch` (a Batch) and the
     per-model packet counts `packets`; returns (best, timings)."""
-    space = space or DEFAULT_SPACE
+    space = space or BATCH_SPACE
     pilot = [max(1, int(n * fraction)) for n in packets]
     first = [PILOT_FIRST_ID] * len(pilot)
     timings = []

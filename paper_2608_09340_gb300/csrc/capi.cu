@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "krl_internal.cuh"
@@ -785,10 +786,10 @@ krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* 
     krl_status ts = resolve_tune(tune, T);
     if (ts != KRL_OK) return ts;
     const unsigned f = b->features;
-    const int maxb = transport_max_block(T.precision, f);
+    const int maxb = transport_batch_max_block();
     if (!T.block) T.block = maxb;
-    else if (T.block > maxb) return fail(KRL_ERR_ARG, "block %d exceeds %d for this walk", T.block, maxb);
-    const int occ = transport_occupancy(T.precision, f, T.block);
+    else if (T.block > maxb) return fail(KRL_ERR_ARG, "block %d exceeds %d for the batched launch", T.block, maxb);
+    const int occ = transport_batch_occupancy(T.precision, f, T.block);
     if (occ < 1) return fail(KRL_ERR_CUDA, "transport kernel cannot be resident at block %d", T.block);
     const int per_sm = T.ctas_per_sm > 0 ? (T.ctas_per_sm < occ ? T.ctas_per_sm : occ) : occ;
     const int grid = b->num_sms * per_sm;
@@ -800,12 +801,19 @@ krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* 
     // the pinned mirror is rewritten here; wait until the previous run's copy
     // has read it (a capture records the copy instead of running it)
     if (!capturing) KRL_CUDA(cudaStreamSynchronize(s), "krl_batch_run");
-    for (size_t m = 0; m < n; ++m) {
-        TransportArgs& A = b->h_args[m];
+    // CTAs take models in slot order: the heaviest (most packets) first, so
+    // that the longest packets start early and the light models fill in
+    // around them; each model keeps its own counters at its own index.
+    std::vector<int> order(n);
+    for (size_t m = 0; m < n; ++m) order[m] = (int)m;
+    std::stable_sort(order.begin(), order.end(), [packets](int x, int y) { return packets[x] > packets[y]; });
+    for (size_t k = 0; k < n; ++k) {
+        const int m = order[k];
+        TransportArgs& A = b->h_args[k];
         A = TransportArgs{};
         fill_args(b->grids[m], A, packets[m], first_ids ? first_ids[m] : 0, seed, T, nullptr);
         A.next = b->d_counts + m;
-        A.stats = b->d_counts + n + m * ST_N;
+        A.stats = b->d_counts + n + (size_t)m * ST_N;
     }
     KRL_CUDA(cudaMemcpyAsync(b->d_args, b->h_args, n * sizeof(TransportArgs), cudaMemcpyHostToDevice, s),
              "upload model arguments");

@@ -159,6 +159,9 @@ cudaError_t launch_transport_ph(const TransportArgs& A, int ph_mode, int precisi
 int transport_occupancy_ph(int ph_mode, int precision, unsigned features, int block);
 // Largest CTA the instantiation is compiled for (512 lean FP32, else 256).
 int transport_max_block(int precision, unsigned features);
+// The batched launch: its CTA size limit and occupancy.
+int transport_batch_max_block();
+int transport_batch_occupancy(int precision, unsigned features, int block);
 
 // ---------------------------------------------------------------- ray trace (raytrace.cu)
 struct RayArgs {

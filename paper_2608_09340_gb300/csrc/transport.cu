@@ -21,6 +21,14 @@ cudaError_t launch_transport_batch(const BatchArgs& B, int precision, unsigned f
                                       : dispatch_batch<float>(B, features, grid, block, s);
 }
 
+int transport_batch_max_block() { return kBatchBlock; }
+
+int transport_batch_occupancy(int precision, unsigned features, int block)
+{
+    return precision == KRL_PREC_FP64 ? batch_occ_dispatch<double>(features, block)
+                                      : batch_occ_dispatch<float>(features, block);
+}
+
 int transport_max_block(int precision, unsigned features)
 {
     return (precision == KRL_PREC_FP32 && !(features & F_RICH)) ? 512 : 256;

@@ -1012,8 +1012,12 @@ __device__ int next_model(const BatchArgs& B)
 // runs its warps on it until its ids run out, drains, and takes the next.
 // CTAs finish models at different times, so one model's tail overlaps the
 // next model's bulk instead of idling the device as separate launches do.
+// The batched launch runs 256-thread CTAs (smaller CTAs move on to the next
+// model sooner; the autotuner found them faster on uneven model sets).
+constexpr int kBatchBlock = 256;
+
 template <typename R, unsigned F>
-__global__ void __launch_bounds__(max_block<R, F>(), 2) k_transport_batch(const __grid_constant__ BatchArgs B)
+__global__ void __launch_bounds__(kBatchBlock, 2) k_transport_batch(const __grid_constant__ BatchArgs B)
 {
     extern __shared__ float sm[];
     __shared__ TransportArgs sA;
@@ -1053,12 +1057,12 @@ cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t
 template <typename R, unsigned F>
 cudaError_t launch_batch_one(const BatchArgs& B, int grid, int block, cudaStream_t s)
 {
-    if (block > max_block<R, F>()) return cudaErrorInvalidConfiguration;
+    if (block > kBatchBlock) return cudaErrorInvalidConfiguration;
     auto kern = k_transport_batch<R, F>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes<R, F>(max_block<R, F>()));
+                                             (int)smem_bytes<R, F>(kBatchBlock));
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -1089,6 +1093,32 @@ cudaError_t dispatch(const TransportArgs& A, unsigned f, int grid, int block, cu
     case 5: return launch_one<R, 5, PH>(A, grid, block, s);
     case 6: return launch_one<R, 6, PH>(A, grid, block, s);
     default: return launch_one<R, 7, PH>(A, grid, block, s);
+    }
+}
+
+template <typename R, unsigned F>
+int batch_occupancy_one(int block)
+{
+    if (block > kBatchBlock) return 0;
+    auto kern = k_transport_batch<R, F>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<R, F>(kBatchBlock));
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem_bytes<R, F>(block)) != cudaSuccess) return 0;
+    return n;
+}
+
+template <typename R>
+int batch_occ_dispatch(unsigned f, int block)
+{
+    switch (f & 7u) {
+    case 0: return batch_occupancy_one<R, 0>(block);
+    case 1: return batch_occupancy_one<R, 1>(block);
+    case 2: return batch_occupancy_one<R, 2>(block);
+    case 3: return batch_occupancy_one<R, 3>(block);
+    case 4: return batch_occupancy_one<R, 4>(block);
+    case 5: return batch_occupancy_one<R, 5>(block);
+    case 6: return batch_occupancy_one<R, 6>(block);
+    default: return batch_occupancy_one<R, 7>(block);
     }
 }
 
