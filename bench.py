@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-raytrace", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-next", action="store_true", help="skip the levels / profile-mode / dusty-slab legs")
     ap.add_argument("--streams", type=int, default=2,
                     help="streams the steps rotate over (1: no overlap of one step's tail with the next)")
     ap.add_argument("--serial", dest="streams", action="store_const", const=1,
@@ -257,6 +258,80 @@ def bench_batch(args, dev):
             "s_batched": t_batch, "s_graph": t_graph, "s_per_model": t_single}
 
 
+def bench_next_rows(args, dev):
+    """Timings of the rows beyond the core pass, each on its own workload:
+    NEXT-2, the Lambda iteration on the config-3 cloud (128^3, 5-level rotor,
+    4 lines; 1e6 packets per line and cycle, scaled from 1e7; 2 cycles);
+    NEXT-3, the Sec. 3.1 slab (a = 0.149, tau_m = 32000, 1e6 packets) in each
+    line-profile mode (mode 1: 2-D table and sampler in global memory; mode
+    2: the slice in shared memory; mode 3: the core-wing blend); NEXT-4, the
+    Sec. 3.2 dusty slab at (a tau0)^{1/3} tau_a = 1 (2e5 packets)."""
+    import dataclasses
+    import math
+    import torch
+    import paper_2608_09340_gb300 as krl
+    import workloads as W
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, r
+
+    # NEXT-2
+    p, n_mol, spec = W.cloud(n=128, packets_per_line=1_000_000)
+    E, gdeg, A, k = spec.arrays()
+    g = krl.Grid(p, device=dev)
+    try:
+        nm = torch.from_numpy(n_mol.reshape(-1)).to(dev)
+        pops = torch.zeros((p.ncell, spec.n_lev), dtype=torch.float64, device=dev)
+        desc = krl.levels_desc(E, gdeg, A, k, spec.mass_amu, nm)
+        g.levels_iterate(desc, 1, 100_000, 1, pops, init_lte=True)          # warm-up
+        n_iter, ppl = 2, 1_000_000
+        dt, ch = timed(lambda: g.levels_iterate(desc, n_iter, ppl, 2, pops, init_lte=True))
+        n_lines = int((A > 0).sum())
+        out["levels"] = {"workload": "cloud 128^3, 5-level rotor, 4 lines", "cycles": n_iter,
+                         "packets_per_line": ppl, "s_per_cycle": dt / n_iter,
+                         "packets_per_s": n_iter * n_lines * ppl / dt,
+                         "max_change": [float(c) for c in ch]}
+    finally:
+        g.close()
+
+    # NEXT-3
+    tau_m = 32000.0
+    base = W.slab(tau0=tau_m / math.sqrt(math.pi), a=0.149, nz=128, n_packets=1_000_000, bins=(-40.0, 40.0, 800))
+    modes = {}
+    for m in (1, 2, 3):
+        q = dataclasses.replace(base, line=dataclasses.replace(base.line, ph_mode=m))
+        g = krl.Grid(q, device=dev)
+        try:
+            g.run(n=100_000, first=1 << 40, want_stats=False)                # warm-up
+            g.reset()
+            dt, st = timed(lambda: g.run(n=1_000_000, first=0)[0])
+            modes[f"ph_mode_{m}"] = {"scat_per_s": st.scatterings / dt, "s": dt}
+        finally:
+            g.close()
+    modes["mode1_over_mode2"] = modes["ph_mode_1"]["scat_per_s"] / modes["ph_mode_2"]["scat_per_s"]
+    out["profile_modes"] = {"workload": "slab 128 cells, a = 0.149, tau_m = 32000, 1e6 packets", **modes}
+
+    # NEXT-4
+    a, tau0 = 0.015, 1e5
+    q = W.dusty_slab(1.0 / (a * tau0) ** (1.0 / 3.0), tau0=tau0, a=a, n_packets=200_000)
+    g = krl.Grid(q, device=dev)
+    try:
+        g.run(n=20_000, first=1 << 40, want_stats=False)
+        g.reset()
+        dt, st = timed(lambda: g.run(n=200_000, first=0)[0])
+        f_esc = float(g.tally("spec_w").sum().item()) / 200_000
+        out["dusty_slab"] = {"workload": "slab a = 0.015, tau0 = 1e5, (a tau0)^1/3 tau_a = 1, 2e5 packets",
+                             "scat_per_s": st.scatterings / dt, "f_esc": f_esc, "absorbed": int(st.absorbed)}
+    finally:
+        g.close()
+    return out
+
+
 def run_reference(args, rank):
     """The FP64 oracle as it stands, on the host cores, a bounded sample per step."""
     if rank != 0:
@@ -452,6 +527,9 @@ def main():
     bt = None
     if rank == 0 and not args.no_batch:
         bt = bench_batch(args, dev)
+    nx = None
+    if rank == 0 and not args.no_next:
+        nx = bench_next_rows(args, dev)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -467,6 +545,7 @@ def main():
                        "parallelism": f"packet-id shards x{world}",
                        "exchange": f"tally all-reduce, {exchange_bytes} bytes per rank" if world > 1 else "none"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "raytrace": rt, "batch": bt,
+            "next_rows": nx, "crossings_per_s": cross_all / t_max,
             "gpu_launches": 2 * args.steps, "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

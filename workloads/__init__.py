@@ -279,6 +279,18 @@ class LevelSpec:
     k_ul: float = 1e-11          # collisional de-excitation, every pair u > l
     mass_amu: float = 28.0
 
+    def arrays(self):
+        """The level data as arrays: energies E_J / k_B = B J (J + 1) [K],
+        degeneracies 2J + 1, A[u][l] (A1 u^3 for l = u - 1, else 0) and the
+        collision coefficients k[u][l] (k_ul for every u > l)."""
+        J = np.arange(self.n_lev, dtype=np.float64)
+        A = np.zeros((self.n_lev, self.n_lev))
+        k = np.zeros((self.n_lev, self.n_lev))
+        for u in range(1, self.n_lev):
+            A[u, u - 1] = self.A1 * u ** 3
+            k[u, :u] = self.k_ul
+        return self.B_K * J * (J + 1.0), 2.0 * J + 1.0, A, k
+
 
 def cloud(n: int = 128, seed: int = 3, mean_n: float = 1e3, sigma_lnrho: float = 1.5, T_K: float = 20.0,
           sigma_v_kms: float = 1.0, abundance: float = 1e-4, box_pc: float = 0.04,
