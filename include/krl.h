@@ -369,6 +369,8 @@ typedef struct {
                                this grid's tally of `camera`                    */
     const float* jline;     /* device [ncell] frequency-integrated line emission
                                per unit path (same units), or NULL              */
+    int no_scratch;         /* nonzero: allocate nothing; evaluate the profile
+                               per segment (slower, same result)                */
 } krl_raytrace_desc;
 
 /*
@@ -382,10 +384,10 @@ typedef struct {
  * j_k = emiss_k + jline H(a, x_k)/sqrt(pi). maps: device float32
  * [n_ch][npix_y][npix_x], written (raw units: emissivity x cell widths).
  * All faces are open for the rays. Enqueued on `s`; does not synchronise.
- * H(a, x_k) depends on the cell and the channel only, so it is tabulated
- * once per call in a stream-ordered scratch of ncell x n_ch floats
- * (cudaMallocAsync on `s`, freed on `s` after the trace); when that memory
- * is not available the trace evaluates H per segment, with the same result.
+ * alpha_k depends on the cell and the channel only, so it is tabulated once
+ * per call in a stream-ordered scratch of ncell x n_ch floats (cudaMallocAsync
+ * on `s`, freed on `s` after the trace); with no_scratch, or when that memory
+ * is not available, the trace evaluates H per segment, with the same result.
  */
 KRL_API krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float* maps, krl_stream s);
 

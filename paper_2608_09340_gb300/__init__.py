@@ -71,7 +71,8 @@ class krl_line_info(C.Structure):
 
 class krl_raytrace_desc(C.Structure):
     _fields_ = [("camera", C.c_int), ("theta", C.c_double), ("phi", C.c_double), ("npix_x", C.c_int),
-                ("npix_y", C.c_int), ("fov_cells", C.c_double), ("emiss", C.c_void_p), ("jline", C.c_void_p)]
+                ("npix_y", C.c_int), ("fov_cells", C.c_double), ("emiss", C.c_void_p), ("jline", C.c_void_p),
+                ("no_scratch", C.c_int)]
 
 
 KRL_MAX_LEVELS = 8
@@ -364,14 +365,14 @@ class Grid:
         return list(ch)[:n_iter]
 
     def raytrace(self, camera: int, npix_x: int, npix_y: int, fov_cells: float, emiss=None, jline=None,
-                 theta: float = 0.0, phi: float = 0.0, stream=None):
+                 theta: float = 0.0, phi: float = 0.0, no_scratch: bool = False, stream=None):
         """Channel maps [n_ch, npix_y, npix_x] (float32 tensor) for one camera."""
         import torch
         nch = self.problem.channels[2]
         maps = torch.empty((nch, npix_y, npix_x), dtype=torch.float32, device=self.device)
         d = krl_raytrace_desc(camera, theta, phi, npix_x, npix_y, fov_cells,
                               emiss.data_ptr() if emiss is not None else None,
-                              jline.data_ptr() if jline is not None else None)
+                              jline.data_ptr() if jline is not None else None, int(bool(no_scratch)))
         krl_raytrace_channels(self.handle, d, maps, stream)
         return maps
 

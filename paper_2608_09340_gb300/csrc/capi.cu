@@ -688,7 +688,7 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
     cudaStream_t s = (cudaStream_t)st;
     const size_t hbytes = (size_t)g->ncell * (size_t)L.n_ch * sizeof(float);
     A.hcube = nullptr;
-    if (cudaMallocAsync((void**)&A.hcube, hbytes, s) != cudaSuccess) {
+    if (!d->no_scratch && cudaMallocAsync((void**)&A.hcube, hbytes, s) != cudaSuccess) {
         (void)cudaGetLastError();
         A.hcube = nullptr;
     }

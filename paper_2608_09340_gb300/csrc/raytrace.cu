@@ -14,9 +14,13 @@
 // alpha_abs is the continuum absorption (zero without one), applied here in
 // the imaging pass as the two-step scheme does (Sec. 3.2).
 //
-// GPU layout: one warp per pixel, channels across lanes, so that a cell's
-// [n_ch] emissivity row is one coalesced read and the walk is shared by the
-// warp. Rays are marched from the camera side backwards; each channel sums
+// GPU layout: per camera, a prep kernel tabulates the channel extinction
+// alpha_k per (cell, channel) (it depends on the cell and the channel only);
+// the trace then gives each ray a group of lanes with the channels across
+// them (4 per lane), so that a cell's [n_ch] rows are coalesced reads and a
+// warp follows several neighbouring rays. Without memory for the cube, one
+// warp per pixel evaluates the profile per segment. Rays are marched from
+// the camera side backwards; each channel sums
 // I = sum_seg T j dl f(dtau) with T = exp(-tau in front of the segment), the
 // optical depth and the sum carried with compensated (Kahan) addition so
 // that FP32 stays within 1e-5 of an FP64 trace over hundreds of segments.
@@ -104,12 +108,12 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v)
 }
 
 // Per-camera profile cube: for every (cell, channel), H(a, x_k) with
-// x_k = -(v_k + n.V)/b. Along one camera direction x_k depends on the cell
+// x_k = -(v_k + n.V)/b, or (ALPHA) the extinction alpha0 H + alpha_abs. Along one camera direction x_k depends on the cell
 // and the channel only, not on the ray, so the trace reads it from here
 // instead of evaluating the profile for each of the ~16 rays that cross a
 // cell. The arithmetic is the trace's own (float-pair n.V, exponent-split
 // table index). One warp per cell, channels across lanes.
-template <int CPL>
+template <int CPL, bool ALPHA>
 __global__ void __launch_bounds__(256) k_rt_profile(const RayArgs A, float* hc)
 {
     __shared__ float sv[kVoigtN];
@@ -143,6 +147,7 @@ __global__ void __launch_bounds__(256) k_rt_profile(const RayArgs A, float* hc)
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncell; c += nwarps) {
         const float4 rec = __ldg(A.cells + c);
+        const float ta = (ALPHA && A.tau_abs) ? __ldg(A.tau_abs + c) : 0.0f;
         float vnh, vnl;
         dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
 #pragma unroll
@@ -150,15 +155,133 @@ __global__ void __launch_bounds__(256) k_rt_profile(const RayArgs A, float* hc)
             const int k = lane + 32 * q;
             if (k < A.n_ch) {
                 const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
-                hc[(size_t)c * A.n_ch + k] = voigt_rt(xk, sv, eI, eF, a, H0);
+                const float H = voigt_rt(xk, sv, eI, eF, a, H0);
+                hc[(size_t)c * A.n_ch + k] = ALPHA ? fmaf(rec.x, H, ta) : H;
             }
         }
     }
 }
 
-// PRE: read H(a, x_k) from the per-camera cube A.hcube (k_rt_profile)
-// instead of evaluating it per segment.
-template <int CPL, bool PRE>
+// (1 - e^{-d})/d and e^{-d} without a branch: the exponential form above
+// d = 0.05, the series below.
+__device__ __forceinline__ float escape_factor_bf(float d)
+{
+    const float e = __expf(-d);
+    const float lg = __fdividef(1.0f - e, d);
+    const float sm = 1.0f - d * (0.5f - d * (1.0f / 6.0f - d * (1.0f / 24.0f - d * (1.0f / 120.0f))));
+    return d > 0.05f ? lg : sm;
+}
+
+// The trace over the per-camera cube (k_rt_profile): LPR lanes per ray, 4
+// channels per lane (lane l of a ray holds channels l + LPR q, q < 4), so a
+// warp follows 32 / LPR neighbouring rays, whose walks through the grid
+// nearly coincide. The per-segment work (face distances, cell index) is
+// shared by fewer lanes' worth of channels than with one ray per warp. The
+// cube holds the extinction alpha0 H + alpha_abs (JL false) or H (JL true:
+// the line-emission term needs H; alpha is formed here).
+template <int LPR, bool JL>
+__global__ void __launch_bounds__(256) k_trace_cube(const RayArgs A)
+{
+    constexpr int CPL = 4;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % LPR;
+    const long long ray = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPR) + lane / LPR;
+    const long long npix = (long long)A.npix_x * A.npix_y;
+    if (ray >= npix) return;                 // no warp-wide operations follow
+    const int ix = (int)(ray % A.npix_x);
+    const int iy = (int)(ray / A.npix_x);
+
+    // ray setup in FP64: pixel centre on the image plane, box entry/exit
+    const double uc = (ix + 0.5) * A.pix - 0.5 * A.pix * A.npix_x;
+    const double vc = (iy + 0.5) * A.pix - 0.5 * A.pix * A.npix_y;
+    double P[3], n[3];
+    for (int d = 0; d < 3; ++d) {
+        P[d] = A.centre[d] + uc * A.u[d] + vc * A.v[d];
+        n[d] = A.n[d];
+    }
+    const double hi[3] = {(double)A.nx, (double)A.ny, (double)A.nz};
+    double t0 = -1e300, t1 = 1e300;
+    bool hit = true;
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] != 0.0) {
+            double ta = (0.0 - P[d]) / n[d], tb = (hi[d] - P[d]) / n[d];
+            t0 = fmax(t0, fmin(ta, tb));
+            t1 = fmin(t1, fmax(ta, tb));
+        } else if (!(P[d] >= 0.0 && P[d] < hi[d])) {
+            hit = false;
+        }
+    }
+    float I[CPL], Ic[CPL], tau[CPL], tc[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) I[q] = Ic[q] = tau[q] = tc[q] = 0.0f;
+
+    if (hit && t1 > t0) {
+        int ci[3];
+        float p[3], dir[3], inv[3];
+        for (int d = 0; d < 3; ++d) {
+            double X = fmin(hi[d], fmax(0.0, P[d] + t1 * n[d]));
+            double f = floor(X);
+            int c = (int)f;
+            double r = X - f;
+            dir[d] = (float)(-n[d]);
+            if (r == 0.0 && dir[d] < 0.0f) { c -= 1; r = 1.0; }
+            if (c >= (int)hi[d]) { c = (int)hi[d] - 1; r = 1.0; }
+            ci[d] = c;
+            p[d] = (float)r;
+            inv[d] = 1.0f / dir[d];
+        }
+        const int max_seg = A.nx + A.ny + A.nz + 3;
+        for (int seg = 0; seg < max_seg; ++seg) {
+            if (ci[0] < 0 || ci[0] >= A.nx || ci[1] < 0 || ci[1] >= A.ny || ci[2] < 0 || ci[2] >= A.nz) break;
+            float s = 3.0e38f;
+            int axis = 0;
+            for (int d = 0; d < 3; ++d) {
+                float t = dir[d] > 0.0f ? (1.0f - p[d]) * inv[d] : (dir[d] < 0.0f ? -p[d] * inv[d] : 3.0e38f);
+                if (t < s) { s = t; axis = d; }
+            }
+            const int c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
+            const float* arow = A.hcube + (size_t)c * A.n_ch;
+            const float* jrow = A.emiss + (size_t)c * A.n_ch;
+            float a0 = 0.0f, ta = 0.0f, jl = 0.0f;
+            if (JL) {
+                a0 = __ldg(A.cells + c).x;
+                ta = A.tau_abs ? __ldg(A.tau_abs + c) : 0.0f;
+                jl = __ldg(A.jline + c) * 0.56418958354775628f;
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const int k = sub + LPR * q;
+                if (k < A.n_ch) {
+                    const float v = __ldg(arow + k);
+                    float j = __ldg(jrow + k);
+                    float alpha = v;
+                    if (JL) {
+                        alpha = fmaf(a0, v, ta);
+                        j = fmaf(jl, v, j);
+                    }
+                    const float dtau = alpha * s;
+                    const float T = __expf(-tau[q]);
+                    kahan_add(I[q], Ic[q], T * j * s * escape_factor_bf(dtau));
+                    kahan_add(tau[q], tc[q], dtau);
+                }
+            }
+            for (int d = 0; d < 3; ++d)
+                if (d != axis) p[d] = fminf(1.0f, fmaxf(0.0f, fmaf(s, dir[d], p[d])));
+            const int step = dir[axis] > 0.0f ? 1 : -1;
+            ci[axis] += step;
+            p[axis] = step > 0 ? 0.0f : 1.0f;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int k = sub + LPR * q;
+        if (k < A.n_ch) A.maps[((size_t)k * A.npix_y + iy) * A.npix_x + ix] = I[q];
+    }
+}
+
+// Without the per-camera cube (its memory not available): one warp per
+// pixel, the profile evaluated per segment.
+template <int CPL>
 __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
 {
     __shared__ float sv[kVoigtN];
@@ -245,23 +368,17 @@ __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
             const int c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
             const float4 rec = __ldg(A.cells + c);
             // n . V/b (|V/b| reaches tens) as a float pair
-            float vnh = 0.0f, vnl = 0.0f;
-            if (!PRE) dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
+            float vnh, vnl;
+            dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
             const float jl = A.jline ? __ldg(A.jline + c) : 0.0f;
             const float ta = A.tau_abs ? __ldg(A.tau_abs + c) : 0.0f;
             const float* jrow = A.emiss + (size_t)c * A.n_ch;
-            const float* hrow = PRE ? A.hcube + (size_t)c * A.n_ch : nullptr;
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
                 const int k = lane + 32 * q;
                 if (k < A.n_ch) {
-                    float H;
-                    if (PRE) {
-                        H = __ldg(hrow + k);
-                    } else {
-                        const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
-                        H = voigt_rt(xk, sv, eI, eF, a, H0);
-                    }
+                    const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
+                    const float H = voigt_rt(xk, sv, eI, eF, a, H0);
                     const float dtau = fmaf(rec.x, H, ta) * s;
                     float j = __ldg(jrow + k);
                     if (A.jline) j = fmaf(jl * 0.56418958354775628f, H, j);
@@ -286,26 +403,39 @@ __global__ void __launch_bounds__(256) k_raytrace(const RayArgs A)
 
 }  // namespace
 
-template <int CPL>
-cudaError_t launch_cpl(const RayArgs& A, long long blocks, int sm_count, cudaStream_t s)
+// The profile cube (when A.hcube), then the trace over it with LPR lanes
+// per ray; without the cube, the one-ray-per-warp trace that evaluates the
+// profile per segment.
+template <int CPL, int LPR>
+cudaError_t launch_cpl(const RayArgs& A, int sm_count, cudaStream_t s)
 {
+    const long long npix = (long long)A.npix_x * A.npix_y;
     if (A.hcube) {
-        k_rt_profile<CPL><<<sm_count * 8, 256, 0, s>>>(A, A.hcube);
-        k_raytrace<CPL, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+        const long long blocks = (npix * LPR + 255) / 256;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        if (A.jline) {
+            k_rt_profile<CPL, false><<<sm_count * 8, 256, 0, s>>>(A, A.hcube);
+            k_trace_cube<LPR, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+        } else {
+            k_rt_profile<CPL, true><<<sm_count * 8, 256, 0, s>>>(A, A.hcube);
+            k_trace_cube<LPR, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+        }
     } else {
-        k_raytrace<CPL, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+        const long long blocks = (npix * 32 + 255) / 256;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        k_raytrace<CPL><<<(unsigned)blocks, 256, 0, s>>>(A);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_raytrace(const RayArgs& A, int sm_count, cudaStream_t s)
 {
-    const long long npix = (long long)A.npix_x * A.npix_y;
-    const long long blocks = (npix * 32 + 255) / 256;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (A.n_ch <= 32) return launch_cpl<1>(A, blocks, sm_count, s);
-    if (A.n_ch <= 64) return launch_cpl<2>(A, blocks, sm_count, s);
-    if (A.n_ch <= 128) return launch_cpl<4>(A, blocks, sm_count, s);
+    if (A.n_ch <= 4) return launch_cpl<1, 1>(A, sm_count, s);
+    if (A.n_ch <= 8) return launch_cpl<1, 2>(A, sm_count, s);
+    if (A.n_ch <= 16) return launch_cpl<1, 4>(A, sm_count, s);
+    if (A.n_ch <= 32) return launch_cpl<1, 8>(A, sm_count, s);
+    if (A.n_ch <= 64) return launch_cpl<2, 16>(A, sm_count, s);
+    if (A.n_ch <= 128) return launch_cpl<4, 32>(A, sm_count, s);
     return cudaErrorInvalidValue;
 }
 

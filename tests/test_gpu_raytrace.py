@@ -31,11 +31,13 @@ def test_raytrace_matches_fp64_on_the_mc_emissivity():
         jline = torch.from_numpy((1e-3 * p.source.rate.reshape(-1)).astype(np.float32)).cuda()
         for m in range(len(p.cameras)):
             for jl in (None, jline):
-                maps = g.raytrace(m, 24, 20, fov_cells=17.0, jline=jl).cpu().numpy()
                 ref = RT.trace_maps(oracle, p, em[m].cpu().numpy(), camera=m, npix_x=24, npix_y=20, fov=17.0,
                                     jline=None if jl is None else jl.cpu().numpy())
                 assert np.abs(ref).max() > 0
-                assert _crit(maps, ref) <= 1e-5, (m, jl is None, _crit(maps, ref))
+                # with the per-camera extinction cube, and without (profile per segment)
+                for ns in (False, True):
+                    maps = g.raytrace(m, 24, 20, fov_cells=17.0, jline=jl, no_scratch=ns).cpu().numpy()
+                    assert _crit(maps, ref) <= 1e-5, (m, jl is None, ns, _crit(maps, ref))
         # an explicit direction with a caller emissivity buffer
         th, ph = math.radians(30.0), math.radians(70.0)
         maps = g.raytrace(-1, 9, 11, fov_cells=20.0, emiss=em[0].contiguous(), theta=th, phi=ph).cpu().numpy()
@@ -72,3 +74,27 @@ def test_thin_slab_two_step_chain():
     shape = np.exp(-((v + 1e5) / b) ** 2)
     assert abs(v[np.argmax(img)] + 1e5) <= dv
     assert np.max(np.abs(img / img.sum() - shape / shape.sum())) / np.max(shape / shape.sum()) < 0.02
+
+
+@pytest.mark.parametrize("n_ch", [3, 8, 20, 33, 64, 100])
+def test_channel_counts_and_lane_groups(n_ch):
+    """Every lanes-per-ray variant of the trace (1 .. 32 lanes, 4 channels
+    each; ragged channel counts) and the per-segment fallback, on a random
+    emissivity through a moving envelope, against the FP64 trace."""
+    krl = need_gpu()
+    import torch
+    p = W.envelope(n=12, n_ch=n_ch, n_packets=1)
+    rng = np.random.default_rng(n_ch)
+    em = torch.from_numpy(rng.random((p.ncell, n_ch), dtype=np.float32)).cuda()
+    th, ph = math.radians(40.0), math.radians(25.0)
+    q = W.envelope(n=12, n_ch=n_ch, n_packets=1)
+    q.cameras = ((th, ph),)
+    ref = RT.trace_maps(oracle, q, em.cpu().numpy(), camera=0, npix_x=13, npix_y=11, fov=14.0)
+    g = krl.Grid(p)
+    try:
+        for ns in (False, True):
+            maps = g.raytrace(-1, 13, 11, fov_cells=14.0, emiss=em, theta=th, phi=ph, no_scratch=ns).cpu().numpy()
+            assert maps.shape == (n_ch, 11, 13)
+            assert _crit(maps, ref) <= 1e-5, (n_ch, ns, _crit(maps, ref))
+    finally:
+        g.close()
