@@ -2,6 +2,7 @@
 
     python -m paper_2608_09340_gb300.profile_cases transport [--tau0 T] [--packets N] [--launches K]
     python -m paper_2608_09340_gb300.profile_cases raytrace [--grid G] [--pixels P] [--channels C]
+    python -m paper_2608_09340_gb300.profile_cases emissivity [--grid G] [--channels C] [--packets N]
 
 Each case sets up its inputs, runs one warm-up launch and then K timed
 launches of the kernel of interest (so a capture can skip the warm-up with
@@ -52,6 +53,30 @@ def transport(args):
                       "scat_per_s": scat / args.launches / ms * 1e3}))
 
 
+def emissivity(args):
+    """The rich walk filling the envelope's emissivity cube (3 cameras)."""
+    import paper_2608_09340_gb300 as krl
+    import workloads as W
+    p = W.envelope(n=args.grid, n_ch=args.channels, n_packets=args.packets)
+    g = krl.Grid(p)
+    try:
+        g.run(n=args.packets // 10, first=1 << 40, want_stats=False)
+        g.reset()
+        k = [0]
+
+        def one():
+            k[0] += 1
+            g.run(n=args.packets, first=k[0] * args.packets, want_stats=False)
+        ms = _timed(one, args.launches)
+        st = g.tally("stats").cpu().numpy()
+    finally:
+        g.close()
+    scat, cross = int(st[4]), int(st[5])
+    print(json.dumps({"case": "emissivity", "grid": args.grid, "channels": args.channels, "packets": args.packets,
+                      "ms_per_launch": ms, "segments_per_s": (scat + cross) / args.launches / ms * 1e3,
+                      "packets_per_s": args.packets / ms * 1e3}))
+
+
 def raytrace(args):
     import paper_2608_09340_gb300 as krl
     import workloads as W
@@ -73,7 +98,7 @@ def main(argv=None):
     if root not in sys.path:
         sys.path.insert(0, root)
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["transport", "raytrace"])
+    ap.add_argument("case", choices=["transport", "raytrace", "emissivity"])
     ap.add_argument("--tau0", type=float, default=3e4)
     ap.add_argument("--vmax", type=float, default=0.0)
     ap.add_argument("--packets", type=int, default=1 << 21)
@@ -84,7 +109,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
-    {"transport": transport, "raytrace": raytrace}[args.case](args)
+    {"transport": transport, "raytrace": raytrace, "emissivity": emissivity}[args.case](args)
 
 
 if __name__ == "__main__":
