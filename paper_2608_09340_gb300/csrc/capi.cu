@@ -60,7 +60,7 @@ struct krl_grid {
     double* lv_gamma = nullptr;          // [kMaxTrans][ncell]
     double* lv_pops0 = nullptr;          // [ncell][kMaxLevels] frozen emission populations
     float* lv_rate = nullptr;            // [ncell] source rate of the current line
-    double* lv_total = nullptr;          // [1]
+    double* lv_total = nullptr;          // [0]: emission total; then its partial sums
     unsigned long long* lv_change = nullptr;
     // line-profile modes 1 and 3 (krl_line_desc.ph_mode)
     float* voigt2d = nullptr;            // [kV2Na][kV2Nx], built once on first use
@@ -878,7 +878,7 @@ krl_status level_scratch(krl_grid* g)
     if (!g->lv_gamma) e = dalloc(&g->lv_gamma, (size_t)kMaxTrans * n);
     if (e == cudaSuccess && !g->lv_pops0) e = dalloc(&g->lv_pops0, (size_t)kMaxLevels * n);
     if (e == cudaSuccess && !g->lv_rate) e = dalloc(&g->lv_rate, n);
-    if (e == cudaSuccess && !g->lv_total) e = dalloc(&g->lv_total, 1);
+    if (e == cudaSuccess && !g->lv_total) e = dalloc(&g->lv_total, levels_sum_scratch_doubles());
     if (e == cudaSuccess && !g->lv_change) e = dalloc(&g->lv_change, 1);
     if (e != cudaSuccess) return cuda_fail(e, "level scratch");
     return KRL_OK;

@@ -200,6 +200,8 @@ struct LevelConst {
 };
 cudaError_t levels_lte(const LevelConst& L, const float* n_mol, int ncell, double* pops, cudaStream_t s);
 cudaError_t levels_field(const double* pops, int ncell, int n_lev, int lev, double scale, float* out, cudaStream_t s);
+// total: device scratch of levels_sum_scratch_doubles() doubles; the sum lands in total[0].
+size_t levels_sum_scratch_doubles();
 cudaError_t levels_sum_rate(const double* pops, int ncell, int n_lev, int u, double A, double* total, cudaStream_t s);
 cudaError_t levels_gamma(const double* exc, int ncell, const double* total, double dx, double sigma0, double n_packets,
                          double* gamma, cudaStream_t s);

@@ -36,19 +36,39 @@ __global__ void k_level_field(const double* pops, int ncell, int n_lev, int lev,
     out[c] = (float)(scale * pops[(size_t)c * n_lev + lev]);
 }
 
-// FP64 sum of n_u A over cells into *total (one block, grid-stride).
-__global__ void k_sum_rate(const double* pops, int ncell, int n_lev, int u, double A, double* total)
+// FP64 sum of n_u A over cells into *total, in a fixed order (so the result
+// does not depend on scheduling): kSumBlocks blocks each sum a grid-strided
+// share into partials[block], then one block sums the partials.
+constexpr int kSumBlocks = 512;
+
+__device__ __forceinline__ double block_sum256(double v, double* sh)
 {
-    __shared__ double sh[256];
-    double s = 0.0;
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) s += pops[(size_t)c * n_lev + u] * A;
-    sh[threadIdx.x] = s;
+    sh[threadIdx.x] = v;
     __syncthreads();
     for (int off = 128; off > 0; off >>= 1) {
         if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *total = sh[0];
+    return sh[0];
+}
+
+__global__ void k_sum_rate_part(const double* pops, int ncell, int n_lev, int u, double A, double* partials)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
+        s += pops[(size_t)c * n_lev + u] * A;
+    const double b = block_sum256(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+__global__ void k_sum_rate_final(const double* partials, int n, double* total)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    const double b = block_sum256(s, sh);
+    if (threadIdx.x == 0) *total = b;
 }
 
 // Gamma_c = (L / N) sigma0 exc_c / dx^2 with L = total * dx^3 photons/s.
@@ -144,9 +164,12 @@ cudaError_t levels_field(const double* pops, int ncell, int n_lev, int lev, doub
     return cudaGetLastError();
 }
 
+size_t levels_sum_scratch_doubles() { return 1 + (size_t)kSumBlocks; }
+
 cudaError_t levels_sum_rate(const double* pops, int ncell, int n_lev, int u, double A, double* total, cudaStream_t s)
 {
-    k_sum_rate<<<1, 256, 0, s>>>(pops, ncell, n_lev, u, A, total);
+    k_sum_rate_part<<<kSumBlocks, 256, 0, s>>>(pops, ncell, n_lev, u, A, total + 1);
+    k_sum_rate_final<<<1, 256, 0, s>>>(total + 1, kSumBlocks, total);
     return cudaGetLastError();
 }
 

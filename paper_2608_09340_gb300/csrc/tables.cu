@@ -95,29 +95,44 @@ __device__ double us_xnode(int i)
 
 // One thread per sampler row: sequential cumulative sum, then ln CDF and
 // the row's search guide.
+// One block per row: the cell masses in parallel, then the normalisation
+// and running sums by one thread in index order (the same sums, in the same
+// order, as a serial build), the logs in parallel, the guide by one thread.
 __global__ void k_usampler(double a, float* xs, float* lncdf, unsigned char* guide)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kUsNx) return;
-    double x = us_xnode(i);
-    xs[i] = (float)x;
-    double tot = 0.0;
-    for (int j = 0; j < kUsNu - 1; ++j) tot += cell_mass(x, a, j);
-    float* row = lncdf + (size_t)i * kUsNu;
-    double run = 0.0;
-    row[0] = (float)log(kUsFloor);
-    for (int j = 1; j < kUsNu; ++j) {
-        run += cell_mass(x, a, j - 1);
-        double C = run / tot;
-        row[j] = (float)log(C > kUsFloor ? C : kUsFloor);
+    __shared__ double mass[kUsNu - 1];
+    __shared__ double cdf[kUsNu];
+    const int i = blockIdx.x;
+    const double x = us_xnode(i);
+    for (int j = threadIdx.x; j < kUsNu - 1; j += blockDim.x) mass[j] = cell_mass(x, a, j);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        xs[i] = (float)x;
+        double tot = 0.0;
+        for (int j = 0; j < kUsNu - 1; ++j) tot += mass[j];
+        double run = 0.0;
+        cdf[0] = 0.0;
+        for (int j = 1; j < kUsNu; ++j) {
+            run += mass[j - 1];
+            cdf[j] = run / tot;
+        }
     }
-    unsigned char* gd = guide + (size_t)i * kGuideN;
-    int j = 0;
-    for (int m = 0; m < kGuideN; ++m) {
-        double w = -kGuideW + 2.0 * kGuideW * m / kGuideN;
-        double lt = -log1p(exp(-w));          // ln sigmoid(w)
-        while (j < kUsNu - 2 && (double)row[j + 1] <= lt) ++j;
-        gd[m] = (unsigned char)j;
+    __syncthreads();
+    float* row = lncdf + (size_t)i * kUsNu;
+    for (int j = threadIdx.x; j < kUsNu; j += blockDim.x) {
+        const double C = cdf[j];
+        row[j] = (float)log(j > 0 && C > kUsFloor ? C : kUsFloor);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned char* gd = guide + (size_t)i * kGuideN;
+        int j = 0;
+        for (int m = 0; m < kGuideN; ++m) {
+            double w = -kGuideW + 2.0 * kGuideW * m / kGuideN;
+            double lt = -log1p(exp(-w));          // ln sigmoid(w)
+            while (j < kUsNu - 2 && (double)row[j + 1] <= lt) ++j;
+            gd[m] = (unsigned char)j;
+        }
     }
 }
 
@@ -301,7 +316,7 @@ cudaError_t build_line_tables(double a, const LineTables& T, bool with_r, cudaSt
     double* coef = T.work;
     k_weideman<<<1, 64, 0, s>>>(coef, N, L);
     k_voigt<<<(kVoigtN + 255) / 256, 256, 0, s>>>(a, coef, N, L, T.voigt_lnH, T.H0);
-    k_usampler<<<1, 64, 0, s>>>(a, T.us_x, T.us_lncdf, T.us_guide);
+    k_usampler<<<kUsNx, 256, 0, s>>>(a, T.us_x, T.us_lncdf, T.us_guide);
     if (with_r) {
         double* p = T.work + 64;
         k_rmasses<<<(kRnX + 127) / 128, 128, 0, s>>>(a, p);
