@@ -1,6 +1,7 @@
 """Many models in one persistent launch (krl_batch_run) give exactly the
-tallies of one krl_run_packets launch per model, also when the batched
-launch is captured into a CUDA graph and replayed."""
+tallies of one krl_run_packets launch per model (one of them with continuum
+absorption), also when the batched launch is captured into a CUDA graph and
+replayed."""
 import numpy as np
 import pytest
 
@@ -15,14 +16,15 @@ def _models():
           W.sphere(vmax_kms=0.0, tau0=2e3, n=16, n_packets=700, tallies=("scatmap",)),
           W.slab(tau0=5e3, a=1e-2, n_packets=1500),
           W.sphere(vmax_kms=-250.0, tau0=1e5, n=32, n_packets=2500, a=1e-3, tallies=("scatmap",)),
-          W.box(tau0=50.0, n=8, n_packets=4000, tallies=("scatmap", "exc"))]
+          W.box(tau0=50.0, n=8, n_packets=4000, tallies=("scatmap", "exc")),
+          W.dusty_slab(0.1, tau0=3e3, n_packets=1500, bins=(-30.0, 30.0, 60))]
     for i, p in enumerate(ms):
         p.seed = 11
     return ms
 
 
 def _tallies(g):
-    out = {k: g.tally(k) for k in ("spec_n", "scatmap", "stats", "exc")}
+    out = {k: g.tally(k) for k in ("spec_n", "spec_w", "scatmap", "stats", "exc", "absw")}
     return {k: (None if v is None else v.cpu().numpy()) for k, v in out.items()}
 
 
@@ -50,6 +52,11 @@ def test_batch_equals_one_launch_per_model():
                 assert np.array_equal(got["scatmap"], ref["scatmap"]), m
             if ref["exc"] is not None:
                 assert np.allclose(got["exc"], ref["exc"], rtol=1e-5), m
+            if ref["absw"] is not None:         # the dusty slab's absorbed weight
+                # (summed in FP32 per cell visit; the visits are cut at the tail
+                # compactions, which differ between launches: as exc, 1e-5)
+                assert np.allclose(got["absw"], ref["absw"], rtol=1e-5, atol=1e-12), m
+            assert np.allclose(got["spec_w"], ref["spec_w"], rtol=1e-9, atol=1e-12), m
             assert st[m].emitted == ms[m].n_packets and st[m].scatterings == ref["stats"][4]
         b.close()
     finally:
