@@ -33,10 +33,14 @@ PACKETS_PER_STEP = JOB_PACKETS
 E2E_MAX_STEPS = 3
 METRIC = "scatterings/s & packets/s (64³ τ0=1e6 sphere)"
 UNIT = "scatterings/s"
-# Algorithmic lane operations per event (derivation in the design doc): a
-# scattering = 2 Philox4x32-10 blocks + sampler inversion + Box-Muller +
-# isotropic direction + R_IIA frequency update + one segment; a face crossing
-# = profile lookup + exit distances + cell step.
+# Algorithmic lane operations per event (the minimum lane instructions the
+# algorithm needs): a scattering = 2 Philox4x32-10 blocks (160: 10 rounds x
+# {2 mul-hi, 2 mul-lo, 2 xor3, 2 key adds}) + 7 uniform conversions (14) +
+# 3 logs, 2 sincos, 2 square roots (16) + sampler row and two row inversions
+# (72) + direction, g, x_out, reciprocals (26) + profile lookup (12) + exit
+# distances (18) + position and decision (12); a face crossing = profile
+# lookup (12) + exit distances (18) + position (9) + cell step and bounds
+# (10) + record load (1).
 OPS_PER_SCAT = 330
 OPS_PER_CROSS = 50
 FP32_LANES_PER_SM = 128
