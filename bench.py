@@ -137,18 +137,23 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_from_profile():
-    """DRAM bytes per launch recorded by the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def profile_figures():
+    """(DRAM bytes per launch, thread instructions per event) recorded by the
+    committed ncu summary, if it was taken on the current kernel source
+    (else None for both)."""
     try:
         txt = open(PROFILE_SUMMARY).read()
         src_hash = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRC)).hexdigest()[:16]
         vals = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith(" "))
         if vals.get("kernel_source_sha256_16", "").strip() != src_hash:
-            return None
-        return float(vals["dram_bytes_per_launch_scaled"].strip())
+            return None, None
+        return float(vals["dram_bytes_per_launch_scaled"].strip()), float(vals["thread_instructions_per_event"].strip())
     except Exception:
-        return None
+        return None, None
+
+
+def traffic_from_profile():
+    return profile_figures()[0]
 
 
 RT_GRID = 256
@@ -528,9 +533,16 @@ def main():
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
     ops = OPS_PER_SCAT * scat + OPS_PER_CROSS * cross
     achieved = ops / kern_s
-    traffic = traffic_from_profile()
+    traffic, inst_per_event = profile_figures()
+    # issue ceiling: every SM sub-partition issuing one warp instruction per
+    # cycle at full SIMT width, over the measured thread instructions per event
+    issue_frac = None
+    if inst_per_event:
+        ceiling = props.multi_processor_count * 4 * 32 * sm_max * 1e6 / inst_per_event
+        issue_frac = (scat_all + cross_all) / t_max / ceiling
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": traffic,
+            "frac": achieved / peak_ops, "traffic": traffic, "issue_ceiling_frac": issue_frac,
+            "thread_instructions_per_event": inst_per_event,
             "launch_ms_mean": sum(launch_ms) / len(launch_ms),
             "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                            f"{sm_max:.0f} MHz ({peak_kind} max SM clock)",
