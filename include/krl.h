@@ -8,7 +8,12 @@
  * angle-dependent partial redistribution sampled from tables (Sec. 2.1.1,
  * 2.1.2, Eq. riia-scatter), and tallies of the escaped spectrum, the
  * excitation rate (Sec. 2.1.3), the velocity-resolved mean intensity and the
- * camera-directed scattering emissivity (Sec. 2.2.1, Eq. scat-line).
+ * camera-directed scattering emissivity (Sec. 2.2.1, Eq. scat-line); the
+ * three line-profile modes (Sec. 2.3.1) and continuum absorption (Sec. 3.2)
+ * in that pass; many models in one persistent launch (krl_batch_*); the
+ * channel-map ray trace of the two-step imaging (Sec. 2.2.2,
+ * krl_raytrace_channels); statistical equilibrium and the Lambda iteration
+ * (Sec. 2.1.3, krl_levels_*).
  *
  * Conventions shared by every call:
  *  - Pointers documented as "device" are CUDA device pointers (for example

@@ -333,7 +333,7 @@ extern "C" {
 
 const char* krl_last_error(void) { return g_err; }
 
-int krl_version(void) { return 100; }
+int krl_version(void) { return 200; }       // 0.2.0: ph_mode, tau_abs, absorbed counts, no_scratch
 
 krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st)
 {
