@@ -33,7 +33,7 @@ constexpr size_t kRtabElems = (size_t)kRnG * kRnX * kRnD;
 // logit(xi) = ln(xi / (1 - xi)) on [-kGuideW, kGuideW]; entry m is the
 // largest node j whose CDF is <= sigmoid(left edge of bin m). A lookup starts
 // there and walks to the exact node, so the guide only shortens the search.
-constexpr int kGuideN = 128;
+constexpr int kGuideN = 256;
 constexpr double kGuideW = 16.7;
 
 // Shared-memory image of the per-line sampling tables used by the walk.
