@@ -46,7 +46,7 @@ OPS_PER_CROSS = 50
 FP32_LANES_PER_SM = 128
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "transport_sphere64_tau1e4.txt")
 KERNEL_SRC = [os.path.join(ROOT, "paper_2608_09340_gb300", "csrc", f)
-              for f in ("transport_impl.cuh", "transport.cu")]
+              for f in ("transport_impl.cuh", "transport.cu", "krl_internal.cuh")]
 
 
 def parse():
