@@ -62,7 +62,7 @@ def test_sphere_full_size(v):
 
 
 def test_fp32_against_fp64_at_large_n():
-    """Config 1's slab at 1e6 packets: the production FP32 walk against the
+    """The tau0 = 1e4, a = 0.01 slab at 1e6 packets: the production FP32 walk against the
     FP64 walk (the instantiation held in lockstep with the oracle), where
     the two-sample noise floor of the 200-bin spectrum is well below 2 %:
     relative L1 < 2 % and chi^2 p > 0.01."""
@@ -75,3 +75,20 @@ def test_fp32_against_fp64_at_large_n():
     assert chi2_two_sample(a, b)[2] > 0.01
     assert f32["stats"].escaped == f64["stats"].escaped == 1_000_000
     assert abs(f32["stats"].scatterings / f64["stats"].scatterings - 1.0) < 0.01
+
+
+def test_velocity_reversal_mirrors_the_spectrum():
+    """With no recoil, reversing every velocity mirrors the problem in
+    frequency (x -> -x and u -> -u leave the Voigt profile, the atom-velocity
+    distribution and R_IIA unchanged), so the outflow spectrum equals the
+    infall spectrum reflected about line centre. Two independent 2e5-packet
+    runs (different seeds) on the 64^3 sphere at +-200 km/s, compared by a
+    two-sample chi^2 of mirrored bins."""
+    krl = need_gpu()
+    n = 200_000
+    out = gpu_run(krl, W.sphere(vmax_kms=200.0, seed=11), krl.KRL_PREC_FP32, n=n, records=False)
+    inn = gpu_run(krl, W.sphere(vmax_kms=-200.0, seed=12), krl.KRL_PREC_FP32, n=n, records=False)
+    a, b = out["spec_n"][1:-1], inn["spec_n"][1:-1][::-1]
+    assert out["spec_n"][0] == inn["spec_n"][-1]
+    assert chi2_two_sample(a, b)[2] > 1e-3
+    assert rel_l1(a, b) < 0.02, rel_l1(a, b)

@@ -210,6 +210,28 @@ def test_outflow_reddens_and_infall_blues(oracle_mod):
     assert red[0] > 0.8 and red[1] < 0.2
 
 
+def test_velocity_reversal_mirrors_the_spectrum(oracle_mod):
+    """No recoil term: v -> -v together with x -> -x maps the problem onto
+    itself (the Voigt profile, the atom-velocity distribution and R_IIA are
+    even), so the outflow spectrum is the infall spectrum reflected about
+    line centre. Independent seeds; a two-sample chi^2 of mirrored bins. A
+    global sign slip flips both spectra and passes here (the red/blue test
+    above catches it); this one catches terms that do not flip with the
+    flow, such as a frequency offset or an asymmetric velocity sampler."""
+    spec = {}
+    for v, seed in ((150.0, 3), (-150.0, 4)):
+        p = W.sphere(vmax_kms=v, tau0=1e4, a=4.7e-4, n=16, n_packets=3000, seed=seed,
+                     bins=(-40.0, 40.0, 80), tallies=())
+        r = oracle_mod.run(p)
+        _conserved(r)
+        assert r["spec_c"][0] == 0 and r["spec_c"][-1] == 0
+        spec[v] = r["spec_c"][1:-1].astype(np.float64)
+    a, b = spec[150.0], spec[-150.0][::-1]
+    keep = (a + b) >= 20
+    stat = np.sum((a[keep] - b[keep]) ** 2 / (a[keep] + b[keep]))
+    assert chi2.sf(stat, keep.sum()) > 1e-3, stat
+
+
 # ------------------------------------------------------------------ emissivity
 
 def test_thin_slab_emissivity_normalisation(oracle_mod):
