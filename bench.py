@@ -163,7 +163,7 @@ RT_CAMERAS = 3
 
 
 def bench_raytrace(args, dev):
-    """Channel maps of the config-5 image: a 256^3 rotating, infalling
+    """Channel maps of the envelope imaging workload: a 256^3 rotating, infalling
     envelope with 64 velocity channels over +-5 km/s, imaged at 1024^2 pixels
     from 3 inclinations (0, 45, 90 deg). The emissivity cube (3 x 256^3 x 64
     FP32) is filled by a Monte Carlo pass of 1e6 packets first; one pass =
@@ -221,7 +221,7 @@ BATCH_TAU = (1e3, 1e5)
 
 
 def bench_batch(args, dev):
-    """Config-4 model set at the scaled size (64 uniform spheres, sides in
+    """The many-model set at the scaled size (64 uniform spheres, sides in
     {32, 48, 64, 96, 128}, tau0 log-uniform in [1e3, 1e5], a log-uniform in
     [1e-4, 1e-2], v_max uniform in [-300, 300] km/s, 3e5 packets split in
     proportion to tau0): one persistent batched launch (launch parameters
@@ -282,11 +282,11 @@ def bench_batch(args, dev):
 
 def bench_next_rows(args, dev):
     """Timings of the rows beyond the core pass, each on its own workload:
-    NEXT-2, the Lambda iteration on the config-3 cloud (128^3, 5-level rotor,
+    statistical equilibrium, the Lambda iteration on the molecular cloud (128^3, 5-level rotor,
     4 lines; 1e6 packets per line and cycle, scaled from 1e7; 2 cycles);
-    NEXT-3, the Sec. 3.1 slab (a = 0.149, tau_m = 32000, 1e6 packets) in each
+    the line-profile modes, the Sec. 3.1 slab (a = 0.149, tau_m = 32000, 1e6 packets) in each
     line-profile mode (mode 1: 2-D table and sampler in global memory; mode
-    2: the slice in shared memory; mode 3: the core-wing blend); NEXT-4, the
+    2: the slice in shared memory; mode 3: the core-wing blend); continuum absorption, the
     Sec. 3.2 dusty slab at (a tau0)^{1/3} tau_a = 1 (2e5 packets)."""
     import dataclasses
     import math
@@ -302,7 +302,7 @@ def bench_next_rows(args, dev):
         torch.cuda.synchronize(dev)
         return time.perf_counter() - t0, r
 
-    # NEXT-2
+    # statistical equilibrium (Lambda iteration)
     p, n_mol, spec = W.cloud(n=128, packets_per_line=1_000_000)
     E, gdeg, A, k = spec.arrays()
     g = krl.Grid(p, device=dev)
@@ -321,7 +321,7 @@ def bench_next_rows(args, dev):
     finally:
         g.close()
 
-    # NEXT-3
+    # line-profile modes
     tau_m = 32000.0
     base = W.slab(tau0=tau_m / math.sqrt(math.pi), a=0.149, nz=128, n_packets=1_000_000, bins=(-40.0, 40.0, 800))
     modes = {}
@@ -370,7 +370,7 @@ def bench_next_rows(args, dev):
     out["paper_table1_box"] = {"workload": "box 32^3, tau0 = 1e3, T = 100 K, a = 4.73e-3, volume source, "
                                            "thermal profile (the paper's timing setup)", "rows": rows}
 
-    # NEXT-4
+    # continuum absorption
     a, tau0 = 0.015, 1e5
     q = W.dusty_slab(1.0 / (a * tau0) ** (1.0 / 3.0), tau0=tau0, a=a, n_packets=200_000)
     g = krl.Grid(q, device=dev)

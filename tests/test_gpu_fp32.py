@@ -11,7 +11,7 @@ from _gpu_common import agreement, chi2_two_sample, gpu_run, need_gpu, rel_l1
 pytestmark = pytest.mark.gpu
 
 
-def test_slab_cfg1_full_config():
+def test_slab_full_size():
     """Static slab, 64 cells, a = 1e-2, line-centre tau0 = 1e4, 1e4 packets,
     200 bins over [-30, 30]: FP32 GPU vs oracle."""
     krl = need_gpu()

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 def _cases():
     c = {}
-    c["slab_cfg1"] = W.slab(tau0=1e4, a=1e-2, n_packets=1000)
+    c["slab_tau1e4"] = W.slab(tau0=1e4, a=1e-2, n_packets=1000)
     c["sphere_outflow"] = W.sphere(vmax_kms=200.0, tau0=1e4, n=16, n_packets=1000)
     c["sphere_infall"] = W.sphere(vmax_kms=-200.0, tau0=1e4, n=16, n_packets=1000)
     rag = W.sphere(tau0=300.0, n=7, n_packets=777)                # odd grid, ragged packet count
