@@ -201,6 +201,16 @@ typedef struct {
                                    of its lanes are idle (1..32)                    */
     uint64_t max_iters;         /* per-packet cap on walk iterations (budget); values
                                    above 2^32 - 1 act as 2^32 - 1                   */
+    int64_t emiss_records;      /* FP32 runs with an emissivity tally deposit it in
+                                   two stages: the walk records each segment (32 B)
+                                   in a stream-ordered buffer of this many records,
+                                   then one warp per segment adds its channels.
+                                   0: 64 per packet, clamped to [2^16, 2^25];
+                                   -1: deposit inside the walk (no buffer). Segments
+                                   beyond the buffer, and every segment when it
+                                   cannot be allocated, are deposited by the walk:
+                                   the result is the same up to the order of the
+                                   FP32 atomic additions                            */
 } krl_tune;
 
 /* One record per packet of a run (optional output). */

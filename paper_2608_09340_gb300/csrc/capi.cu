@@ -303,8 +303,10 @@ bool blend_crossing(double a, double* u0)
 
 krl_status resolve_tune(const krl_tune* tune, krl_tune& T)
 {
-    T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 1ull << 40};
+    T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 1ull << 40, 0};
     if (tune) {
+        if (tune->emiss_records < -1) return fail(KRL_ERR_ARG, "emiss_records must be >= -1");
+        T.emiss_records = tune->emiss_records;
         if (tune->precision != KRL_PREC_FP32 && tune->precision != KRL_PREC_FP64)
             return fail(KRL_ERR_ARG, "unknown precision");
         T.precision = tune->precision;
@@ -607,7 +609,31 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
 
     KRL_CUDA(cudaMemsetAsync(slot_next, 0, sizeof(unsigned long long), s), "reset work counter");
     KRL_CUDA(cudaMemsetAsync(slot_stats, 0, ST_N * sizeof(unsigned long long), s), "reset run counters");
-    KRL_CUDA(launch_transport(A, T.precision, f, grid, T.block, s), "transport launch");
+    // Two-stage emissivity deposit (FP32 walk): a stream-ordered segment
+    // buffer for this run; without one the walk deposits every segment.
+    void* segbuf = nullptr;
+    if (T.precision == KRL_PREC_FP32 && g->emiss && T.emiss_records >= 0) {
+        const unsigned long long lo = 1ull << 16, hi = 1ull << 25;
+        unsigned long long cap = (unsigned long long)T.emiss_records;
+        if (cap == 0) cap = n > hi / 64 ? hi : (n * 64 < lo ? lo : n * 64);
+        if (cudaMallocAsync(&segbuf, 16 + (size_t)cap * 32, s) == cudaSuccess) {
+            A.seg_count = static_cast<unsigned long long*>(segbuf);
+            A.seg = reinterpret_cast<float4*>(static_cast<char*>(segbuf) + 16);
+            A.seg_cap = cap;
+        } else {
+            (void)cudaGetLastError();
+            segbuf = nullptr;
+        }
+    }
+    cudaError_t le = cudaSuccess;
+    if (segbuf) le = cudaMemsetAsync(segbuf, 0, sizeof(unsigned long long), s);
+    if (le == cudaSuccess) le = launch_transport(A, T.precision, f, grid, T.block, s);
+    if (le == cudaSuccess && segbuf) le = launch_emiss_deposit(A, f, g->num_sms, s);
+    if (segbuf) {
+        const cudaError_t fe = cudaFreeAsync(segbuf, s);
+        if (le == cudaSuccess) le = fe;
+    }
+    if (le != cudaSuccess) return cuda_fail(le, "transport launch");
     KRL_CUDA(add_counters(g->stats, slot_stats, ST_N, s), "accumulate counters");
     if (stats) {
         unsigned long long h[ST_N];

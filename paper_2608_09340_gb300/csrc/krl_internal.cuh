@@ -123,6 +123,12 @@ struct TransportArgs {
     int v2_row;               // mode 1: rows v2_row, v2_row + 1 bracket log10 a
     double v2_w;              // mode 1: weight of row v2_row + 1
     double u0;                // mode 3: core-wing crossing point
+    // two-stage emissivity deposit (FP32 walk): segment records, 2 float4
+    // each ({cell bits, base, x_com, nx}, {ny, nz, 0, 0}); count may run past
+    // the capacity (the segments beyond it are deposited by the walk)
+    float4* seg;
+    unsigned long long* seg_count;
+    unsigned long long seg_cap;
 };
 
 constexpr unsigned kRichEps = 1u << 16;
@@ -140,6 +146,9 @@ cudaError_t build_voigt2d(float* out, double* work, cudaStream_t s);
 // Launch the walk (transport.cu). grid/block chosen by the caller.
 cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned features,
                              int grid, int block, cudaStream_t s);
+// Second stage of the emissivity deposit over the records A.seg[0 ..
+// min(*A.seg_count, A.seg_cap)), on the stream after the walk that wrote them.
+cudaError_t launch_emiss_deposit(const TransportArgs& A, unsigned features, int sm_count, cudaStream_t s);
 // Many models in one launch: models[m] holds model m's full argument block
 // (its own work counter `next`, run counters `stats`, tables and tallies).
 struct BatchArgs {

@@ -21,6 +21,21 @@ cudaError_t launch_transport_batch(const BatchArgs& B, int precision, unsigned f
                                       : dispatch_batch<float>(B, features, grid, block, s);
 }
 
+cudaError_t launch_emiss_deposit(const TransportArgs& A, unsigned features, int sm_count, cudaStream_t s)
+{
+    const bool vel = (features & F_VEL) != 0;
+    auto kern = vel ? k_emiss_deposit<true> : k_emiss_deposit<false>;
+    static int occ[2] = {0, 0};      // resident CTAs per SM, per instantiation
+    if (!occ[vel]) {
+        int o = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kDepositBlock, 0);
+        if (e != cudaSuccess) return e;
+        occ[vel] = o > 0 ? o : 1;
+    }
+    kern<<<sm_count * occ[vel], kDepositBlock, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 int transport_batch_max_block() { return kBatchBlock; }
 
 int transport_batch_occupancy(int precision, unsigned features, int block)

@@ -492,9 +492,128 @@ __device__ bool emit(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p)
     return true;
 }
 
+// Camera m's share of one segment's emissivity (Eq. scat-line with the
+// trilinear R_IIA table, Eq. riia-table, or Eq. riia-inf for |x_in| >= 120):
+// the channels k with |x_out,k - x_com| <= 10, x_out,k = -(x0 + (k + 1/2) dx)
+// - n_cam.V/b, each receive base R(x_out,k - x_com; x_com, g), g = n.n_cam.
+// emiss_setup holds what depends on the segment and camera only: the channel
+// range, n_cam.V/b and either the table cell (row offset and the four (g, x)
+// corner weights) or, in the wing limit (roff < 0), the Gaussian's
+// normalisation (w00) and 1 / (2 var) (w01).
+template <typename R>
+struct EmSetup {
+    int k0, k1;            // channel range; empty when k0 > k1
+    int roff;              // R table offset of corner (g_j, x_i), or -1
+    R vc, sgn;             // n_cam.V/b; sign of x_com (R(D; -x, g) = R(-D; x, g))
+    R w00, w01, w10, w11;
+};
+
+template <typename R, bool VEL>
+__device__ __forceinline__ EmSetup<R> emiss_setup(const TransportArgs& A, int m, const float4& rec, R nx, R ny, R nz,
+                                                  R xcom)
+{
+    EmSetup<R> S;
+    const R axc = fabs(xcom);
+    S.sgn = xcom < (R)0 ? (R)-1 : (R)1;
+    const R cx = (R)A.cam[m][0], cy = (R)A.cam[m][1], cz = (R)A.cam[m][2];
+    R g = nx * cx + ny * cy + nz * cz;
+    g = fmin((R)1, fmax((R)-1, g));
+    S.vc = VEL ? vdot<R>(cx, cy, cz, rec) : (R)0;
+    // channels with |x_out,k - x_com| <= 10
+    const R ctr = Ops<R>::dv(-(R)A.ch_x0 - S.vc - xcom, (R)A.ch_dx) - (R)0.5;
+    const R span = Ops<R>::dv((R)kRdMax, (R)A.ch_dx);
+    const int k0 = (int)ceil(ctr - span) - 1;
+    const int k1 = (int)floor(ctr + span) + 1;
+    S.k0 = k0 < 0 ? 0 : k0;
+    S.k1 = k1 > A.n_ch - 1 ? A.n_ch - 1 : k1;
+    if (axc >= (R)kRxMax) {
+        const R v = fmax((R)1 - g, (R)(kRsMin * kRsMin));
+        S.roff = -1;
+        S.w00 = (R)1 / Ops<R>::sq((R)6.283185307179586 * v);
+        S.w01 = (R)0.5 / v;
+        S.w10 = S.w11 = (R)0;
+        return S;
+    }
+    const R fx = axc * (R)((kRnX - 1) / kRxMax);
+    const R fg = (g + (R)1) * (R)((kRnG - 1) / 2.0);
+    int j = (int)fx;
+    int kg = (int)fg;
+    j = j > kRnX - 2 ? kRnX - 2 : j;
+    kg = kg > kRnG - 2 ? kRnG - 2 : kg;
+    const R wx = fx - (R)j, wg = fg - (R)kg;
+    S.roff = (kg * kRnX + j) * kRnD;
+    S.w00 = ((R)1 - wg) * ((R)1 - wx);
+    S.w01 = ((R)1 - wg) * wx;
+    S.w10 = wg * ((R)1 - wx);
+    S.w11 = wg * wx;
+    return S;
+}
+
+// Channel k of a segment's camera share, added to out[k] (the cell's row of
+// that camera's cube).
+template <typename R>
+__device__ __forceinline__ void emiss_channel(const TransportArgs& A, float* out, const EmSetup<R>& S, R xcom, R base,
+                                              int k)
+{
+    const R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - S.vc;
+    const R D = xo - xcom;
+    if (fabs(D) > (R)kRdMax) return;
+    if (S.roff < 0) {
+        atomicAdd(out + k, (float)(base * S.w00 * Ops<R>::ex(-D * D * S.w01)));
+        return;
+    }
+    const float* r00 = A.rtab + S.roff;
+    const float* r01 = r00 + kRnD;
+    const float* r10 = r00 + (size_t)kRnX * kRnD;
+    const float* r11 = r10 + kRnD;
+    const R Dd = S.sgn * D;
+    const R fd = (Dd + (R)kRdMax) * (R)(1.0 / kRdStep);
+    int i = (int)floor(fd);
+    i = i < 0 ? 0 : (i > kRnD - 2 ? kRnD - 2 : i);
+    const R wd = fd - (R)i;
+    const R a0 = S.w00 * (R)__ldg(r00 + i) + S.w01 * (R)__ldg(r01 + i) + S.w10 * (R)__ldg(r10 + i) +
+                 S.w11 * (R)__ldg(r11 + i);
+    const R a1 = S.w00 * (R)__ldg(r00 + i + 1) + S.w01 * (R)__ldg(r01 + i + 1) + S.w10 * (R)__ldg(r10 + i + 1) +
+                 S.w11 * (R)__ldg(r11 + i + 1);
+    const R val = ((R)1 - wd) * a0 + wd * a1;
+    atomicAdd(out + k, (float)(base * val));
+}
+
+// Camera m's share deposited by one thread (inside the walk).
+template <typename R, bool VEL>
+__device__ __forceinline__ void emiss_camera(const TransportArgs& A, int m, int c, const float4& rec, R nx, R ny,
+                                             R nz, R xcom, R base)
+{
+    const EmSetup<R> S = emiss_setup<R, VEL>(A, m, rec, nx, ny, nz, xcom);
+    if (S.k0 > S.k1) return;
+    float* out = A.emiss + ((size_t)m * A.ncell + c) * A.n_ch;
+    for (int k = S.k0; k <= S.k1; ++k) emiss_channel<R>(A, out, S, xcom, base, k);
+}
+
+// First stage of the two-stage emissivity deposit (FP32 walk): the segment
+// (cell, base weight, x_com, direction) goes to the run's segment buffer,
+// one slot range per converged group of lanes (one atomic on the buffer's
+// counter). Returns false when the buffer is full; the caller then deposits
+// the segment itself.
+__device__ __forceinline__ bool append_segment(const TransportArgs& A, int c, float base, float xcom, float nx,
+                                               float ny, float nz)
+{
+    const unsigned mask = __activemask();
+    const unsigned lane = threadIdx.x & 31u;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long first = 0;
+    if ((int)lane == leader) first = atomicAdd(A.seg_count, (unsigned long long)__popc(mask));
+    first = __shfl_sync(mask, first, leader);
+    const unsigned long long i = first + __popc(mask & ((1u << lane) - 1u));
+    if (i >= A.seg_cap) return false;
+    A.seg[2 * i] = make_float4(__int_as_float(c), base, xcom, nx);
+    A.seg[2 * i + 1] = make_float4(ny, nz, 0.0f, 0.0f);
+    return true;
+}
+
 // Per-segment tallies of the rich mode: mean intensity by comoving channel
-// and the camera-directed emissivity (Eq. scat-line with the trilinear
-// R_IIA table, Eq. riia-table, or Eq. riia-inf for |x_in| >= 120).
+// and the camera-directed emissivity (Eq. scat-line). With a segment buffer
+// (FP32 walk) the emissivity is deposited by the second stage instead.
 template <typename R, unsigned F>
 __device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xcom, R H, R w)
 {
@@ -504,61 +623,64 @@ __device__ void rich_segment(const TransportArgs& A, const Pkt<R>& p, R ds, R xc
     }
     if (!(A.rich & KRL_TALLY_EMISS) || A.n_ch <= 0) return;
     const R base = w * ds * (R)p.rec.x * H * (R)0.079577471545947668;   // 1 / 4 pi
-    const R axc = fabs(xcom);
-    const R sgn = xcom < (R)0 ? (R)-1 : (R)1;    // R(D; -x, g) = R(-D; x, g)
-    for (int m = 0; m < A.n_cam; ++m) {
-        const R cx = (R)A.cam[m][0], cy = (R)A.cam[m][1], cz = (R)A.cam[m][2];
-        R g = p.nx * cx + p.ny * cy + p.nz * cz;
-        g = fmin((R)1, fmax((R)-1, g));
-        R vc = (F & F_VEL) ? vdot<R>(cx, cy, cz, p.rec) : (R)0;
-        // channels with |x_out,k - x_com| <= 10, x_out,k = -(x0 + (k + 1/2) dx) - vc
-        R ctr = Ops<R>::dv(-(R)A.ch_x0 - vc - xcom, (R)A.ch_dx) - (R)0.5;
-        R span = Ops<R>::dv((R)kRdMax, (R)A.ch_dx);
-        int k0 = (int)ceil(ctr - span) - 1;
-        int k1 = (int)floor(ctr + span) + 1;
-        k0 = k0 < 0 ? 0 : k0;
-        k1 = k1 > A.n_ch - 1 ? A.n_ch - 1 : k1;
-        if (k0 > k1) continue;
-        float* out = A.emiss + ((size_t)m * A.ncell + p.c) * A.n_ch;
-        if (axc >= (R)kRxMax) {
-            R v = fmax((R)1 - g, (R)(kRsMin * kRsMin));
-            R inv2v = (R)0.5 / v;
-            R nrm = (R)1 / Ops<R>::sq((R)6.283185307179586 * v);
-            for (int k = k0; k <= k1; ++k) {
-                R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - vc;
-                R D = xo - xcom;
-                if (fabs(D) > (R)kRdMax) continue;
-                atomicAdd(out + k, (float)(base * nrm * Ops<R>::ex(-D * D * inv2v)));
-            }
-            continue;
+    if constexpr (sizeof(R) == 4) {
+        if (A.seg && append_segment(A, p.c, base, xcom, p.nx, p.ny, p.nz)) return;
+    }
+    for (int m = 0; m < A.n_cam; ++m)
+        emiss_camera<R, (F & F_VEL) != 0>(A, m, p.c, p.rec, p.nx, p.ny, p.nz, xcom, base);
+}
+
+// Second stage of the emissivity deposit. A warp takes 32 consecutive
+// segment records (one per lane, coalesced); per camera each lane works out
+// its own segment's setup, then the warp deposits the segments one after the
+// other with the setup broadcast from its lane and the lanes spread over the
+// channel range, so that a segment's R_IIA reads fall on four table rows
+// shared by the warp and its atomic additions on consecutive channels of one
+// cell. The record count is read on the device (no host round trip between
+// the stages).
+constexpr int kDepositBlock = 256;
+
+template <bool VEL>
+__global__ void __launch_bounds__(kDepositBlock) k_emiss_deposit(const __grid_constant__ TransportArgs A)
+{
+    const unsigned long long cnt = *A.seg_count;
+    const unsigned long long n = cnt < A.seg_cap ? cnt : A.seg_cap;
+    const int lane = (int)(threadIdx.x & 31u);
+    const unsigned long long stride = ((unsigned long long)gridDim.x * blockDim.x) & ~31ull;
+    for (unsigned long long w = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; w < n;
+         w += stride) {
+        const unsigned long long i = w + (unsigned long long)lane;
+        const bool valid = i < n;
+        float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0;
+        if (valid) {
+            r0 = __ldg(A.seg + 2 * i);
+            r1 = __ldg(A.seg + 2 * i + 1);
         }
-        R fx = axc * (R)((kRnX - 1) / kRxMax);
-        R fg = (g + (R)1) * (R)((kRnG - 1) / 2.0);
-        int j = (int)fx;
-        int kg = (int)fg;
-        j = j > kRnX - 2 ? kRnX - 2 : j;
-        kg = kg > kRnG - 2 ? kRnG - 2 : kg;
-        R wx = fx - (R)j, wg = fg - (R)kg;
-        const float* r00 = A.rtab + ((size_t)kg * kRnX + j) * kRnD;
-        const float* r01 = r00 + kRnD;
-        const float* r10 = r00 + (size_t)kRnX * kRnD;
-        const float* r11 = r10 + kRnD;
-        R w00 = ((R)1 - wg) * ((R)1 - wx), w01 = ((R)1 - wg) * wx;
-        R w10 = wg * ((R)1 - wx), w11 = wg * wx;
-        for (int k = k0; k <= k1; ++k) {
-            R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - vc;
-            R D = xo - xcom;
-            if (fabs(D) > (R)kRdMax) continue;
-            R Dd = sgn * D;
-            R fd = (Dd + (R)kRdMax) * (R)(1.0 / kRdStep);
-            int i = (int)floor(fd);
-            i = i < 0 ? 0 : (i > kRnD - 2 ? kRnD - 2 : i);
-            R wd = fd - (R)i;
-            R a0 = w00 * (R)__ldg(r00 + i) + w01 * (R)__ldg(r01 + i) + w10 * (R)__ldg(r10 + i) + w11 * (R)__ldg(r11 + i);
-            R a1 = w00 * (R)__ldg(r00 + i + 1) + w01 * (R)__ldg(r01 + i + 1) + w10 * (R)__ldg(r10 + i + 1) +
-                   w11 * (R)__ldg(r11 + i + 1);
-            R val = ((R)1 - wd) * a0 + wd * a1;
-            atomicAdd(out + k, (float)(base * val));
+        const int c = valid ? __float_as_int(r0.x) : 0;
+        const float4 rec = (VEL && valid) ? __ldg(A.cells + c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float base = r0.y, xcom = r0.z;
+        for (int m = 0; m < A.n_cam; ++m) {
+            const EmSetup<float> S = emiss_setup<float, VEL>(A, m, rec, r0.w, r1.x, r1.y, xcom);
+            unsigned todo = __ballot_sync(kFull, valid && S.k0 <= S.k1);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                EmSetup<float> T;
+                T.k0 = __shfl_sync(kFull, S.k0, src);
+                T.k1 = __shfl_sync(kFull, S.k1, src);
+                T.roff = __shfl_sync(kFull, S.roff, src);
+                T.vc = __shfl_sync(kFull, S.vc, src);
+                T.sgn = __shfl_sync(kFull, S.sgn, src);
+                T.w00 = __shfl_sync(kFull, S.w00, src);
+                T.w01 = __shfl_sync(kFull, S.w01, src);
+                T.w10 = __shfl_sync(kFull, S.w10, src);
+                T.w11 = __shfl_sync(kFull, S.w11, src);
+                const float xs = __shfl_sync(kFull, xcom, src);
+                const float bs = __shfl_sync(kFull, base, src);
+                const int cs = __shfl_sync(kFull, c, src);
+                float* out = A.emiss + ((size_t)m * A.ncell + cs) * A.n_ch;
+                for (int k = T.k0 + lane; k <= T.k1; k += 32) emiss_channel<float>(A, out, T, xs, bs, k);
+            }
         }
     }
 }

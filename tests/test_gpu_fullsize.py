@@ -83,12 +83,13 @@ def test_velocity_reversal_mirrors_the_spectrum():
     distribution and R_IIA unchanged), so the outflow spectrum equals the
     infall spectrum reflected about line centre. Two independent 2e5-packet
     runs (different seeds) on the 64^3 sphere at +-200 km/s, compared by a
-    two-sample chi^2 of mirrored bins."""
+    two-sample chi^2 of mirrored bins (the relative L1 distance of two such
+    histograms is ~3 % from counting noise alone, so it is no criterion
+    here)."""
     krl = need_gpu()
     n = 200_000
     out = gpu_run(krl, W.sphere(vmax_kms=200.0, seed=11), krl.KRL_PREC_FP32, n=n, records=False)
     inn = gpu_run(krl, W.sphere(vmax_kms=-200.0, seed=12), krl.KRL_PREC_FP32, n=n, records=False)
-    a, b = out["spec_n"][1:-1], inn["spec_n"][1:-1][::-1]
-    assert out["spec_n"][0] == inn["spec_n"][-1]
+    # full histograms: the underflow bin of one mirrors the overflow of the other
+    a, b = out["spec_n"], inn["spec_n"][::-1]
     assert chi2_two_sample(a, b)[2] > 1e-3
-    assert rel_l1(a, b) < 0.02, rel_l1(a, b)
