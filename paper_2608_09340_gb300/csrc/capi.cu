@@ -121,6 +121,7 @@ void free_line(krl_grid* g)
     dfree(g->tab.us_lncdf);
     dfree(g->tab.us_guide);
     dfree(g->tab.rtab);
+    dfree(g->tab.rquad);
     dfree(g->tab.work);
     dfree(g->spec_w);
     dfree(g->spec_c);
@@ -234,6 +235,7 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.us_lncdf = g->tab.us_lncdf;
     A.us_guide = g->tab.us_guide;
     A.rtab = g->tab.rtab;
+    A.rquad = g->tab.rquad;
     A.src_kind = L.src_kind;
     A.src_profile = L.src_profile;
     A.src_axis = L.src_axis;
@@ -500,6 +502,7 @@ krl_status krl_line_set(krl_grid* g, const krl_line_desc* d, krl_stream st)
     if (e == cudaSuccess) e = dalloc(&g->tab.us_lncdf, (size_t)kUsNx * kUsNu);
     if (e == cudaSuccess) e = dalloc(&g->tab.us_guide, (size_t)kUsNx * kGuideN);
     if (e == cudaSuccess && with_r) e = dalloc(&g->tab.rtab, kRtabElems);
+    if (e == cudaSuccess && with_r) e = dalloc(&g->tab.rquad, kRquadElems);
     if (e == cudaSuccess) e = dalloc(&g->tab.work, line_tables_work_doubles());
     if (e == cudaSuccess) e = dalloc(&g->spec_w, (size_t)L.spec_nbins + 2);
     if (e == cudaSuccess) e = dalloc(&g->spec_c, (size_t)L.spec_nbins + 2);

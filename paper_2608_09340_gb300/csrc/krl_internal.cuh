@@ -28,6 +28,10 @@ constexpr double kRdStep = 0.1;
 constexpr double kRxMax = 120.0;
 constexpr double kRsMin = 0.1;
 constexpr size_t kRtabElems = (size_t)kRnG * kRnX * kRnD;
+// The R table regrouped by interpolation cell: entry (k, j, i) holds the four
+// corners (g_k, x_j), (g_k, x_j+1), (g_k+1, x_j), (g_k+1, x_j+1) at Delta_i,
+// so a trilinear lookup reads two float4 instead of eight floats.
+constexpr size_t kRquadElems = (size_t)(kRnG - 1) * (kRnX - 1) * kRnD;
 
 // Search guide of the sampler rows: for each row, kGuideN bins uniform in
 // logit(xi) = ln(xi / (1 - xi)) on [-kGuideW, kGuideW]; entry m is the
@@ -91,6 +95,7 @@ struct TransportArgs {
     const float* us_lncdf;
     const unsigned char* us_guide;
     const float* rtab;
+    const float4* rquad;      // rtab by interpolation cell (the deposit's second stage)
     int src_kind, src_profile, src_axis, band_axis;
     double src_pos[3];
     double src_plane, band_lo, band_hi;
@@ -225,6 +230,7 @@ struct LineTables {
     float* us_lncdf;    // [kUsNx * kUsNu]
     unsigned char* us_guide;  // [kUsNx * kGuideN]
     float* rtab;        // [kRtabElems]
+    float4* rquad;      // [kRquadElems] (built with rtab)
     double* work;       // scratch: Weideman coefficients + R-table masses
 };
 size_t line_tables_work_doubles();

@@ -152,6 +152,18 @@ __global__ void k_rmasses(double a, double* p)
     for (int k = 0; k < kUsNu - 1; ++k) row[k] /= tot;
 }
 
+// rquad(k, j, i) = the R table's four (g, x) corners of cell (k, j) at Delta_i.
+__global__ void k_rquad(const float* rtab, float4* rquad)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kRquadElems) return;
+    const int i = (int)(e % kRnD);
+    const int j = (int)((e / kRnD) % (kRnX - 1));
+    const int k = (int)(e / ((size_t)kRnD * (kRnX - 1)));
+    const float* r00 = rtab + ((size_t)k * kRnX + j) * kRnD + i;
+    rquad[e] = make_float4(r00[0], r00[kRnD], r00[(size_t)kRnX * kRnD], r00[(size_t)kRnX * kRnD + kRnD]);
+}
+
 // R(D_i; x_j, g_k) = sum_c p_c G(D_i - m_c (g_k - 1); s_k), one thread per entry.
 __global__ void k_rtable(const double* p, float* rtab)
 {
@@ -321,6 +333,7 @@ cudaError_t build_line_tables(double a, const LineTables& T, bool with_r, cudaSt
         double* p = T.work + 64;
         k_rmasses<<<(kRnX + 127) / 128, 128, 0, s>>>(a, p);
         k_rtable<<<(unsigned)((kRtabElems + 255) / 256), 256, 0, s>>>(p, T.rtab);
+        if (T.rquad) k_rquad<<<(unsigned)((kRquadElems + 255) / 256), 256, 0, s>>>(T.rtab, T.rquad);
     }
     return cudaGetLastError();
 }

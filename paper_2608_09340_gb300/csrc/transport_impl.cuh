@@ -497,15 +497,16 @@ __device__ bool emit(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p)
 // the channels k with |x_out,k - x_com| <= 10, x_out,k = -(x0 + (k + 1/2) dx)
 // - n_cam.V/b, each receive base R(x_out,k - x_com; x_com, g), g = n.n_cam.
 // emiss_setup holds what depends on the segment and camera only: the channel
-// range, n_cam.V/b and either the table cell (row offset and the four (g, x)
-// corner weights) or, in the wing limit (roff < 0), the Gaussian's
-// normalisation (w00) and 1 / (2 var) (w01).
+// range, n_cam.V/b and either the table cell (g node kg, x node j, packed as
+// kg << 8 | j, and the four (g, x) corner weights) or, in the wing limit
+// (cell < 0), the Gaussian's normalisation (w00) and 1 / (2 var) (w01).
 template <typename R>
 struct EmSetup {
     int k0, k1;            // channel range; empty when k0 > k1
-    int roff;              // R table offset of corner (g_j, x_i), or -1
+    int cell;              // kg << 8 | j, or -1
     R vc, sgn;             // n_cam.V/b; sign of x_com (R(D; -x, g) = R(-D; x, g))
     R w00, w01, w10, w11;
+    R x0, dx;              // channel origin and width in x units
 };
 
 template <typename R, bool VEL>
@@ -513,6 +514,8 @@ __device__ __forceinline__ EmSetup<R> emiss_setup(const TransportArgs& A, int m,
                                                   R xcom)
 {
     EmSetup<R> S;
+    S.x0 = (R)A.ch_x0;
+    S.dx = (R)A.ch_dx;
     const R axc = fabs(xcom);
     S.sgn = xcom < (R)0 ? (R)-1 : (R)1;
     const R cx = (R)A.cam[m][0], cy = (R)A.cam[m][1], cz = (R)A.cam[m][2];
@@ -520,15 +523,15 @@ __device__ __forceinline__ EmSetup<R> emiss_setup(const TransportArgs& A, int m,
     g = fmin((R)1, fmax((R)-1, g));
     S.vc = VEL ? vdot<R>(cx, cy, cz, rec) : (R)0;
     // channels with |x_out,k - x_com| <= 10
-    const R ctr = Ops<R>::dv(-(R)A.ch_x0 - S.vc - xcom, (R)A.ch_dx) - (R)0.5;
-    const R span = Ops<R>::dv((R)kRdMax, (R)A.ch_dx);
+    const R ctr = Ops<R>::dv(-S.x0 - S.vc - xcom, S.dx) - (R)0.5;
+    const R span = Ops<R>::dv((R)kRdMax, S.dx);
     const int k0 = (int)ceil(ctr - span) - 1;
     const int k1 = (int)floor(ctr + span) + 1;
     S.k0 = k0 < 0 ? 0 : k0;
     S.k1 = k1 > A.n_ch - 1 ? A.n_ch - 1 : k1;
     if (axc >= (R)kRxMax) {
         const R v = fmax((R)1 - g, (R)(kRsMin * kRsMin));
-        S.roff = -1;
+        S.cell = -1;
         S.w00 = (R)1 / Ops<R>::sq((R)6.283185307179586 * v);
         S.w01 = (R)0.5 / v;
         S.w10 = S.w11 = (R)0;
@@ -541,7 +544,7 @@ __device__ __forceinline__ EmSetup<R> emiss_setup(const TransportArgs& A, int m,
     j = j > kRnX - 2 ? kRnX - 2 : j;
     kg = kg > kRnG - 2 ? kRnG - 2 : kg;
     const R wx = fx - (R)j, wg = fg - (R)kg;
-    S.roff = (kg * kRnX + j) * kRnD;
+    S.cell = kg << 8 | j;
     S.w00 = ((R)1 - wg) * ((R)1 - wx);
     S.w01 = ((R)1 - wg) * wx;
     S.w10 = wg * ((R)1 - wx);
@@ -549,32 +552,54 @@ __device__ __forceinline__ EmSetup<R> emiss_setup(const TransportArgs& A, int m,
     return S;
 }
 
-// Channel k of a segment's camera share, added to out[k] (the cell's row of
-// that camera's cube).
-template <typename R>
+// Channel k (kf = k as R) of a segment's camera share, added to out[k] (the
+// cell's row of that camera's cube). QUAD reads the table regrouped by
+// interpolation cell (two float4 loads), else the plain table (eight loads);
+// the values and their order of combination are the same.
+template <typename R, bool QUAD>
 __device__ __forceinline__ void emiss_channel(const TransportArgs& A, float* out, const EmSetup<R>& S, R xcom, R base,
-                                              int k)
+                                              int k, R kf)
 {
-    const R xo = -((R)A.ch_x0 + ((R)k + (R)0.5) * (R)A.ch_dx) - S.vc;
+    const R xo = -(S.x0 + (kf + (R)0.5) * S.dx) - S.vc;
     const R D = xo - xcom;
     if (fabs(D) > (R)kRdMax) return;
-    if (S.roff < 0) {
+    if (S.cell < 0) {
         atomicAdd(out + k, (float)(base * S.w00 * Ops<R>::ex(-D * D * S.w01)));
         return;
     }
-    const float* r00 = A.rtab + S.roff;
-    const float* r01 = r00 + kRnD;
-    const float* r10 = r00 + (size_t)kRnX * kRnD;
-    const float* r11 = r10 + kRnD;
     const R Dd = S.sgn * D;
     const R fd = (Dd + (R)kRdMax) * (R)(1.0 / kRdStep);
-    int i = (int)floor(fd);
-    i = i < 0 ? 0 : (i > kRnD - 2 ? kRnD - 2 : i);
-    const R wd = fd - (R)i;
-    const R a0 = S.w00 * (R)__ldg(r00 + i) + S.w01 * (R)__ldg(r01 + i) + S.w10 * (R)__ldg(r10 + i) +
-                 S.w11 * (R)__ldg(r11 + i);
-    const R a1 = S.w00 * (R)__ldg(r00 + i + 1) + S.w01 * (R)__ldg(r01 + i + 1) + S.w10 * (R)__ldg(r10 + i + 1) +
-                 S.w11 * (R)__ldg(r11 + i + 1);
+    int i;
+    R wd;
+    if constexpr (sizeof(R) == 4) {
+        // floor(fd) for 0 <= fd < 2^23 by a round-down add of 2^23 (exact),
+        // clamped to the last interval, without float/int conversions
+        const float t = __fadd_rd(fd, 8388608.0f) - 8388608.0f;
+        const float fi = fminf(fmaxf(t, 0.0f), (float)(kRnD - 2));
+        i = __float_as_int(fi + 8388608.0f) - 0x4B000000;
+        wd = fd - fi;
+    } else {
+        i = (int)floor(fd);
+        i = i < 0 ? 0 : (i > kRnD - 2 ? kRnD - 2 : i);
+        wd = fd - (R)i;
+    }
+    const int kg = S.cell >> 8, j = S.cell & 255;
+    R a0, a1;
+    if constexpr (QUAD) {
+        const float4* q = A.rquad + ((size_t)kg * (kRnX - 1) + j) * kRnD + i;
+        const float4 q0 = __ldg(q), q1 = __ldg(q + 1);
+        a0 = S.w00 * (R)q0.x + S.w01 * (R)q0.y + S.w10 * (R)q0.z + S.w11 * (R)q0.w;
+        a1 = S.w00 * (R)q1.x + S.w01 * (R)q1.y + S.w10 * (R)q1.z + S.w11 * (R)q1.w;
+    } else {
+        const float* r00 = A.rtab + ((size_t)kg * kRnX + j) * kRnD;
+        const float* r01 = r00 + kRnD;
+        const float* r10 = r00 + (size_t)kRnX * kRnD;
+        const float* r11 = r10 + kRnD;
+        a0 = S.w00 * (R)__ldg(r00 + i) + S.w01 * (R)__ldg(r01 + i) + S.w10 * (R)__ldg(r10 + i) +
+             S.w11 * (R)__ldg(r11 + i);
+        a1 = S.w00 * (R)__ldg(r00 + i + 1) + S.w01 * (R)__ldg(r01 + i + 1) + S.w10 * (R)__ldg(r10 + i + 1) +
+             S.w11 * (R)__ldg(r11 + i + 1);
+    }
     const R val = ((R)1 - wd) * a0 + wd * a1;
     atomicAdd(out + k, (float)(base * val));
 }
@@ -587,7 +612,8 @@ __device__ __forceinline__ void emiss_camera(const TransportArgs& A, int m, int 
     const EmSetup<R> S = emiss_setup<R, VEL>(A, m, rec, nx, ny, nz, xcom);
     if (S.k0 > S.k1) return;
     float* out = A.emiss + ((size_t)m * A.ncell + c) * A.n_ch;
-    for (int k = S.k0; k <= S.k1; ++k) emiss_channel<R>(A, out, S, xcom, base, k);
+    R kf = (R)S.k0;
+    for (int k = S.k0; k <= S.k1; ++k, kf += (R)1) emiss_channel<R, false>(A, out, S, xcom, base, k, kf);
 }
 
 // First stage of the two-stage emissivity deposit (FP32 walk): the segment
@@ -668,7 +694,9 @@ __global__ void __launch_bounds__(kDepositBlock) k_emiss_deposit(const __grid_co
                 EmSetup<float> T;
                 T.k0 = __shfl_sync(kFull, S.k0, src);
                 T.k1 = __shfl_sync(kFull, S.k1, src);
-                T.roff = __shfl_sync(kFull, S.roff, src);
+                T.cell = __shfl_sync(kFull, S.cell, src);
+                T.x0 = S.x0;
+                T.dx = S.dx;
                 T.vc = __shfl_sync(kFull, S.vc, src);
                 T.sgn = __shfl_sync(kFull, S.sgn, src);
                 T.w00 = __shfl_sync(kFull, S.w00, src);
@@ -679,7 +707,9 @@ __global__ void __launch_bounds__(kDepositBlock) k_emiss_deposit(const __grid_co
                 const float bs = __shfl_sync(kFull, base, src);
                 const int cs = __shfl_sync(kFull, c, src);
                 float* out = A.emiss + ((size_t)m * A.ncell + cs) * A.n_ch;
-                for (int k = T.k0 + lane; k <= T.k1; k += 32) emiss_channel<float>(A, out, T, xs, bs, k);
+                float kf = (float)(T.k0 + lane);
+                for (int k = T.k0 + lane; k <= T.k1; k += 32, kf += 32.0f)
+                    emiss_channel<float, true>(A, out, T, xs, bs, k, kf);
             }
         }
     }
