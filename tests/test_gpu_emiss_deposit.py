@@ -7,6 +7,7 @@ the rest), on a moving grid and a static one (the two instantiations of the
 second stage), and through the R_IIA wing limit (Eq. riia-inf, |x_com| >=
 120) against the oracle."""
 import dataclasses
+import math
 
 import numpy as np
 import pytest
@@ -101,3 +102,24 @@ def test_emiss_records_is_validated():
             g.run(n=10, emiss_records=-2)
     finally:
         g.close()
+
+
+def test_channel_sum_is_the_path_length_estimator():
+    """The two-stage cube summed over channels (times the channel width in
+    x and 4 pi) equals alpha0 times the excitation tally, per camera and
+    cell, and the scattering map agrees with it within counting noise (the
+    oracle's pin of the same identity is in test_oracle_walk.py)."""
+    krl = need_gpu()
+    p = W.box(tau0=2.0, n=8, T_K=100.0, n_packets=200_000, tallies=("emiss", "exc", "scatmap"))
+    b = math.sqrt(2.0 * 1.380649e-16 * 100.0 / (W.HYDROGEN_AMU * 1.66053906660e-24))
+    p = dataclasses.replace(p, channels=(-14.0 * b, 0.25 * b, 112),
+                            cameras=((0.0, 0.0), (math.pi / 2, 0.0), (math.pi / 3, 1.0)))
+    out = gpu_run(krl, p, krl.KRL_PREC_FP32, records=False)
+    em = out["emiss"].reshape(3, p.ncell, 112).astype(np.float64)
+    S = em.sum(axis=2) * 0.25 * 4.0 * math.pi
+    P = p.opacity.reshape(-1).astype(np.float64) * out["exc"]
+    assert np.all(np.abs(S.sum(axis=1) / P.sum() - 1.0) < 1e-3)
+    assert np.all(np.abs(S / P - 1.0) < 5e-3)
+    n_scat = float(out["scatmap"].sum())
+    assert abs(n_scat - P.sum()) < 4.0 * math.sqrt(n_scat), (n_scat, P.sum())
+

@@ -256,3 +256,35 @@ def test_thin_slab_emissivity_normalisation(oracle_mod):
     assert abs(S.sum() * dx / (E.sum() * dx) - 1) < 0.02                 # integral, 2%
     assert np.max(np.abs(S / S.sum() - E / E.sum())) / np.max(E / E.sum()) < 0.02   # shape
     assert abs(v[np.argmax(S)] + 1e5) <= dv                               # peak at v = -v_z
+
+
+def _estimator_box(n_packets=20000):
+    """Static 8^3 box, centre-to-face depth 2, T = 100 K, thermal volume
+    source; channels cover x_out in [-14, 14] at 0.25 (wider than x_com +-10
+    for every segment that matters), three cameras."""
+    p = W.box(tau0=2.0, n=8, T_K=100.0, n_packets=n_packets, tallies=("emiss", "exc", "scatmap"))
+    b = math.sqrt(2.0 * 1.380649e-16 * 100.0 / (W.HYDROGEN_AMU * 1.66053906660e-24))
+    return dataclasses.replace(p, channels=(-14.0 * b, 0.25 * b, 112),
+                               cameras=((0.0, 0.0), (math.pi / 2, 0.0), (math.pi / 3, 1.0)))
+
+
+def test_emissivity_channel_sum_is_the_path_length_estimator(oracle_mod):
+    """Two estimators of the scattering rate (Eq. scat-line). Summed over
+    channels (times the channel width in x and 4 pi), each camera's
+    emissivity in a cell is sum w ds alpha0 H times the integral of R over
+    Delta, which is 1: so it equals alpha0 times the excitation tally, cell by
+    cell (to the Riemann sum of R over channels), for every camera. That
+    path-length estimator and the collision estimator (the scattering map)
+    have the same expectation, the number of scatterings."""
+    p = _estimator_box()
+    r = oracle_mod.run(p)
+    assert abs(r["b"] / (p.channels[1] / 0.25) - 1.0) < 1e-12
+    ncam, nch = len(p.cameras), p.channels[2]
+    em = r["emiss"].reshape(ncam, p.ncell, nch)
+    S = em.sum(axis=2) * 0.25 * 4.0 * math.pi              # [cam, cell]
+    P = p.opacity.reshape(-1).astype(np.float64) * r["exc"]  # alpha0 sum w ds H
+    assert np.all(np.abs(S.sum(axis=1) / P.sum() - 1.0) < 1e-3)
+    assert np.all(np.abs(S / P - 1.0) < 5e-3)
+    n_scat = float(r["scat"].sum())
+    assert abs(n_scat - P.sum()) < 4.0 * math.sqrt(n_scat), (n_scat, P.sum())
+
