@@ -209,8 +209,9 @@ def bench_raytrace(args, dev):
             "mc_fill": {"packets": p.n_packets, "s": fill_s, "packets_per_s": p.n_packets / fill_s,
                         "scatterings_per_s": fst.scatterings / fill_s,
                         "segments_per_s": (fst.scatterings + fst.crossings) / fill_s,
-                        "note": "each segment adds up to ~17 channels x 3 cameras of R_IIA-weighted "
-                                "emissivity (FP32 atomics) plus excitation and J"},
+                        "note": "rich walk (excitation, J, destruction) recording each segment, then "
+                                "the two-stage deposit: per segment up to ~20 channels x 3 cameras of "
+                                "R_IIA-weighted emissivity (FP32 atomics); host-timed incl. the stats read"},
             "min_hbm_gbs": cube / ms / 1e6,               # the emissivity cube read once per pass
             "l2": "inputs larger than L2 (emissivity 12.9 GB per pass)"}
 
