@@ -240,6 +240,10 @@ typedef struct {
  * Up to 8 runs of one grid may be in flight at once on different streams
  * (each takes the next of 8 scratch slots in turn); tallies accumulate
  * atomically, so their order does not matter beyond FP64 rounding.
+ * An FP32 run of a line with an emissivity tally also allocates and frees
+ * its segment buffer in stream order on `s` (cudaMallocAsync / cudaFreeAsync,
+ * size set by krl_tune.emiss_records), so the call stays capturable in a
+ * CUDA graph; the buffer is the run's own and never outlives it.
  */
 KRL_API krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t seed,
                            const krl_tune* tune, krl_packet_record* records,
