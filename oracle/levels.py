@@ -114,37 +114,51 @@ def rotor(n_lev: int = 5, B_K: float = 2.77, A1: float = 1e-7, k_ul: float = 1e-
     return Levels(E_K=B_K * J * (J + 1.0), g=2.0 * J + 1.0, A=A, k_coll=k, mass_amu=mass_amu)
 
 
+def gamma_rates(oracle_mod, problem, lev: Levels, pops, pops0, packets_per_line: int, seed: int, cycle: int = 0,
+                nthreads=None):
+    """Gamma_lu per cell for every radiative pair (u, l): one pass of the
+    oracle's FP64 walk per line, with the line's opacity from the lower-level
+    populations `pops` and its emission frozen at `pops0` (a volume source of
+    n_u A_ul per cell, thermal profile), packet ids starting at
+    (cycle * n_lines + line) * N. The path-length estimator: Gamma =
+    (L / N) sigma0 sum(w ds H) / V_cell, with L = sum n_u A_ul V_cell the
+    line's photon rate and ds in cm (the excitation tally holds ds in cell
+    widths, hence one factor dx against V_cell = dx^3)."""
+    import dataclasses as dc
+    trans = lev.transitions()
+    dx = problem.cell_cm
+    gam = {}
+    for t, (u, l) in enumerate(trans):
+        rate = (pops0[:, u] * lev.A[u, l]).astype(np.float32)
+        line = dc.replace(problem.line, nu0_hz=lev.nu(u, l), mass_amu=lev.mass_amu, A_ul=lev.A[u, l],
+                          g_u=lev.g[u], g_l=lev.g[l], k_ul=lev.k_coll[u, l], a_fixed=0.0)
+        q = dc.replace(problem, opacity_kind="n_l",
+                       opacity=pops[:, l].astype(np.float32).reshape(problem.shape), line=line,
+                       source=dc.replace(problem.source, kind="volume", profile="gaussian",
+                                         rate=rate.reshape(problem.shape)),
+                       tallies=("exc",), spectrum=(-40.0, 40.0, 80), channels=None, cameras=())
+        r = oracle_mod.run(q, n=packets_per_line, first=(cycle * len(trans) + t) * packets_per_line, seed=seed,
+                           nthreads=nthreads)
+        b = T.doppler_b(problem.T_K, lev.mass_amu)
+        s0 = T.sigma0(lev.g[u], lev.g[l], lev.A[u, l], lev.nu(u, l), b)
+        lum = float(np.sum(pops0[:, u] * lev.A[u, l])) * dx ** 3
+        gam[(u, l)] = lum / packets_per_line * s0 * r["exc"] / dx ** 2
+    return gam
+
+
 def lambda_iterate(oracle_mod, problem, n_mol, lev: Levels, n_iter: int, packets_per_line: int, seed: int,
                    pops=None, nthreads=None):
     """The Lambda iteration with the oracle's FP64 walk, following the same
     packet ids per cycle and line ((cycle * n_lines + line) * N), so that a
     device run with the same inputs follows the same random streams.
     Returns (populations [ncell, n], per-cycle max change / n_mol)."""
-    import dataclasses as dc
     n_mol = np.asarray(n_mol, dtype=np.float32).astype(np.float64).reshape(-1)
     n_coll = np.asarray(problem.n_coll, dtype=np.float32).astype(np.float64).reshape(-1)
     pops = boltzmann(lev, problem.T_K, n_mol) if pops is None else np.array(pops, dtype=np.float64)
     pops0 = pops.copy()
-    trans = lev.transitions()
-    dx = problem.cell_cm
     changes = []
     for it in range(n_iter):
-        gam = {}
-        for t, (u, l) in enumerate(trans):
-            rate = (pops0[:, u] * lev.A[u, l]).astype(np.float32)
-            line = dc.replace(problem.line, nu0_hz=lev.nu(u, l), mass_amu=lev.mass_amu, A_ul=lev.A[u, l],
-                              g_u=lev.g[u], g_l=lev.g[l], k_ul=lev.k_coll[u, l], a_fixed=0.0)
-            q = dc.replace(problem, opacity_kind="n_l",
-                           opacity=pops[:, l].astype(np.float32).reshape(problem.shape), line=line,
-                           source=dc.replace(problem.source, kind="volume", profile="gaussian",
-                                             rate=rate.reshape(problem.shape)),
-                           tallies=("exc",), spectrum=(-40.0, 40.0, 80), channels=None, cameras=())
-            r = oracle_mod.run(q, n=packets_per_line, first=(it * len(trans) + t) * packets_per_line, seed=seed,
-                               nthreads=nthreads)
-            b = T.doppler_b(problem.T_K, lev.mass_amu)
-            s0 = T.sigma0(lev.g[u], lev.g[l], lev.A[u, l], lev.nu(u, l), b)
-            lum = float(np.sum(pops0[:, u] * lev.A[u, l])) * dx ** 3
-            gam[(u, l)] = lum / packets_per_line * s0 * r["exc"] / dx ** 2
+        gam = gamma_rates(oracle_mod, problem, lev, pops, pops0, packets_per_line, seed, it, nthreads)
         new = solve(lev, problem.T_K, n_coll, n_mol, gam)
         with np.errstate(invalid="ignore", divide="ignore"):
             ch = np.where(n_mol[:, None] > 0, np.abs(new - pops) / n_mol[:, None], 0.0)
