@@ -107,7 +107,8 @@ def test_volume_source_follows_the_rate(oracle_mod):
 def test_single_scattering_probability(oracle_mod):
     """Point source at the centre of a uniform cube of line-centre depth
     tau_c per cell: P(escape unscattered) = < exp(-tau_c H(a,0) d(n)) >_n
-    with d(n) = 2 / max|n_i| the distance to the cube surface (4^3 cells)."""
+    with d(n) = 2 / max|n_i| the distance to the cube surface (4^3 cells);
+    also with the opacity given as a lower-level density."""
     tc = 0.2
     a = 1e-2
     p = W.sphere(n=4, tau0=1.0, a=a, tallies=(), n_packets=100000)
@@ -126,6 +127,16 @@ def test_single_scattering_probability(oracle_mod):
     val = np.exp(-tc * H0 * d)
     expect = np.sum(val * mu[1][:, None]) / 2.0 / ph.size
     assert abs(frac - expect) < 4 * math.sqrt(expect * (1 - expect) / 100000)
+    # the same cube with the opacity given as the lower-level density:
+    # alpha0 dx = n_l sigma0 dx (Sec. 2.1, Eq. sigma0) must give the same walk
+    from oracle import tables as OT
+    b = OT.doppler_b(p.T_K, p.line.mass_amu)
+    s0 = OT.sigma0(p.line.g_u, p.line.g_l, p.line.A_ul, p.line.nu0_hz, b)
+    q = dataclasses.replace(p, opacity_kind="n_l",
+                            opacity=np.full((4, 4, 4), tc / (s0 * p.cell_cm), np.float32))
+    rq = oracle_mod.run(q, records=True)
+    fq = np.mean(rq["records"]["nscat"] == 0)
+    assert abs(fq - expect) < 4 * math.sqrt(expect * (1 - expect) / 100000)
 
 
 # ------------------------------------------------------------------ destruction, budget
