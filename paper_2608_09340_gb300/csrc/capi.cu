@@ -337,7 +337,7 @@ extern "C" {
 
 const char* krl_last_error(void) { return g_err; }
 
-int krl_version(void) { return 200; }       // 0.2.0: ph_mode, tau_abs, absorbed counts, no_scratch
+int krl_version(void) { return 300; }       // 0.3.0: krl_tune.emiss_records (two-stage deposit)
 
 krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st)
 {
