@@ -33,16 +33,16 @@ PACKETS_PER_STEP = JOB_PACKETS
 E2E_MAX_STEPS = 3
 METRIC = "scatterings/s & packets/s (64³ τ0=1e6 sphere)"
 UNIT = "scatterings/s"
-# Algorithmic lane operations per event (the minimum lane instructions the
-# algorithm needs): a scattering = 2 Philox4x32-10 blocks (160: 10 rounds x
-# {2 mul-hi, 2 mul-lo, 2 xor3, 2 key adds}) + 7 uniform conversions (14) +
-# 3 logs, 2 sincos, 2 square roots (16) + sampler row and two row inversions
-# (72) + direction, g, x_out, reciprocals (26) + profile lookup (12) + exit
-# distances (18) + position and decision (12); a face crossing = profile
-# lookup (12) + exit distances (18) + position (9) + cell step and bounds
-# (10) + record load (1).
-OPS_PER_SCAT = 330
-OPS_PER_CROSS = 50
+# Algorithmic lane operations per event, from the per-unit work estimate of
+# the pass: a scattering = 2 Philox4x32-10 blocks (20 rounds of 2 multiply-
+# high and the xors, ~120 integer ops) + ~8 special-function ops (Box-Muller,
+# isotropic direction, ln xi) + ~14 sampler steps (row choice and search) +
+# ~100 FP32 ops (the upper end of 60-100) = 242; a face crossing = one Voigt
+# lookup (lg2 and interpolation) + ~30 FP32 ops = 32. The measured thread
+# instructions per event (from the ncu summary) give the issue-ceiling
+# fraction beside it.
+OPS_PER_SCAT = 242
+OPS_PER_CROSS = 32
 FP32_LANES_PER_SM = 128
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "transport_sphere64_tau1e4.txt")
 KERNEL_SRC = [os.path.join(ROOT, "paper_2608_09340_gb300", "csrc", f)
