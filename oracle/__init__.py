@@ -10,7 +10,11 @@ shares no code with it.
 * ``oracle.run``        - derive the per-cell inputs from a workload Problem
   and run packets through the C walk.
 * ``oracle.raytrace``   - FP64 formal solution for channel maps.
-* ``oracle.levels``     - FP64 statistical-equilibrium solves.
+* ``oracle.levels``     - FP64 statistical-equilibrium solves and the Lambda
+  iteration's excitation rates.
+* ``oracle.exact``      - O-exact: the static-slab walk with no tables (the
+  Voigt function evaluated directly, exact velocity draws), to measure the
+  tabulated method's table error.
 """
 from __future__ import annotations
 
