@@ -206,7 +206,8 @@ typedef struct {
                                    in a stream-ordered buffer of this many records,
                                    then one warp per segment adds its channels.
                                    0: 64 per packet, clamped to [2^16, 2^25];
-                                   -1: deposit inside the walk (no buffer). Segments
+                                   -1: deposit inside the walk (no buffer); at most
+                                   2^36 (KRL_ERR_ARG beyond). Segments
                                    beyond the buffer, and every segment when it
                                    cannot be allocated, are deposited by the walk:
                                    the result is the same up to the order of the

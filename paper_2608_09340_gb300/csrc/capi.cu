@@ -307,7 +307,8 @@ krl_status resolve_tune(const krl_tune* tune, krl_tune& T)
 {
     T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 1ull << 40, 0};
     if (tune) {
-        if (tune->emiss_records < -1) return fail(KRL_ERR_ARG, "emiss_records must be >= -1");
+        if (tune->emiss_records < -1 || tune->emiss_records > (1ll << 36))
+            return fail(KRL_ERR_ARG, "emiss_records must be in [-1, 2^36]");
         T.emiss_records = tune->emiss_records;
         if (tune->precision != KRL_PREC_FP32 && tune->precision != KRL_PREC_FP64)
             return fail(KRL_ERR_ARG, "unknown precision");
