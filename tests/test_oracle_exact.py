@@ -34,16 +34,22 @@ def test_exact_sampler_follows_the_quadrature_cdf(a, x):
     assert dev < 1.95 / math.sqrt(n), dev             # the 0.1 % Kolmogorov-Smirnov bound
 
 
-def test_tabulated_walk_matches_the_exact_walk():
-    """Static slab, line-centre tau0 = 500, a = 0.01, 4000 packets each:
-    two-sample chi^2 of the spectra p > 1e-3 and mean |x| within 4 sigma."""
+@pytest.mark.parametrize("tau0,a,nz,n,bins", [
+    (500.0, 0.01, 64, 4000, (-20.0, 20.0, 80)),
+    (2000.0 / math.sqrt(math.pi), 0.149, 128, 3000, (-30.0, 30.0, 120)),   # Sec. 3.1's slab at tau_m = 2000
+])
+def test_tabulated_walk_matches_the_exact_walk(tau0, a, nz, n, bins):
+    """Static slab, line-centre photons at the midplane: a core-dominated
+    case (a = 0.01) and the paper's damped slab (a = 0.149, whose photons
+    escape through the core-wing transition). Two-sample chi^2 of the
+    spectra p > 1e-3 and mean |x| within 4 sigma."""
     from _gpu_common import chi2_two_sample
-    tau0, a, n, bins = 500.0, 0.01, 4000, (-20.0, 20.0, 80)
     ex = E.slab_spectrum(tau0, a, n, 2, bins)
-    tab = oracle.run(W.slab(tau0=tau0, a=a, n_packets=n, bins=bins))["spec_c"]
+    tab = oracle.run(W.slab(tau0=tau0, a=a, nz=nz, n_packets=n, bins=bins))["spec_c"]
     assert ex.sum() == tab.sum() == n
     assert chi2_two_sample(ex[1:-1], tab[1:-1])[2] > 1e-3
-    x = np.linspace(-20.0, 20.0, 81)[:-1] + 0.25
+    lo, hi, nb = bins
+    x = lo + (np.arange(nb) + 0.5) * (hi - lo) / nb
     stats = []
     for c in (ex[1:-1].astype(np.float64), tab[1:-1].astype(np.float64)):
         m = (np.abs(x) * c).sum() / c.sum()
