@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="krl", choices=["krl", "reference"])
-    ap.add_argument("--packets", type=int, default=PACKETS_PER_STEP)
-    ap.add_argument("--tau0", type=float, default=1e6,
-                    help="centre-to-edge line-centre depth (1e6 is the benchmark; smaller for profiling)")
+    ap.add_argument("--packets", type=int, default=None,
+                    help=f"packets per step (default {PACKETS_PER_STEP}; 2^21 for --profile-case)")
+    ap.add_argument("--tau0", type=float, default=None,
+                    help="centre-to-edge line-centre depth (default 1e6, the benchmark; 3e4 for --profile-case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-raytrace", action="store_true")
@@ -67,6 +68,17 @@ def parse():
                     help="streams the steps rotate over (1: no overlap of one step's tail with the next)")
     ap.add_argument("--serial", dest="streams", action="store_const", const=1,
                     help="same as --streams 1")
+    ap.add_argument("--no-serial-leg", action="store_true",
+                    help="skip the one-stream job timed after the main leg")
+    # small fixed cases of one kernel for profiler captures (no bench line)
+    ap.add_argument("--profile-case", choices=["transport", "raytrace", "emissivity"], default=None,
+                    help="run one small case of a kernel (a warm-up launch, then --launches timed "
+                         "launches) and print its CUDA-event time per launch instead of the bench line")
+    ap.add_argument("--vmax", type=float, default=0.0, help="profile case: sphere v_max [km/s]")
+    ap.add_argument("--grid", type=int, default=128, help="profile case: envelope grid side")
+    ap.add_argument("--pixels", type=int, default=512, help="profile case: image side in pixels")
+    ap.add_argument("--channels", type=int, default=64, help="profile case: velocity channels")
+    ap.add_argument("--launches", type=int, default=1, help="profile case: timed launches")
     return ap.parse_args()
 
 
@@ -387,6 +399,88 @@ def bench_next_rows(args, dev):
     return out
 
 
+# ------------------------------------------------------------------ profiler cases
+#
+# Each case sets up its inputs, runs one warm-up launch and then --launches
+# timed launches of the kernel of interest (so that a capture can skip the
+# warm-up with `-s 1`), and prints the CUDA-event time per launch. The
+# defaults keep a few GB at most on the device:
+#
+#   python bench.py --profile-case transport [--tau0 T] [--vmax V] [--packets N] [--launches K]
+#   python bench.py --profile-case raytrace [--grid G] [--pixels P] [--channels C]
+#   python bench.py --profile-case emissivity [--grid G] [--channels C] [--packets N]
+
+def _timed_launches(fn, k):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(k):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def profile_case(args):
+    import torch
+    import paper_2608_09340_gb300 as krl
+    import workloads as W
+    torch.cuda.set_device(0)
+    k = [0]
+    if args.profile_case == "transport":
+        p = W.sphere(vmax_kms=args.vmax, tau0=args.tau0)
+        g = krl.Grid(p)
+        try:
+            g.run(n=args.packets, first=0, want_stats=False)
+            g.reset()
+
+            def one():
+                k[0] += 1
+                g.run(n=args.packets, first=k[0] * args.packets, want_stats=False)
+            ms = _timed_launches(one, args.launches)
+            st = g.tally("stats").cpu().numpy()
+        finally:
+            g.close()
+        scat, cross = int(st[4]), int(st[5])
+        out = {"case": "transport", "tau0": args.tau0, "vmax_kms": args.vmax, "packets": args.packets,
+               "ms_per_launch": ms, "scatterings_per_launch": scat / args.launches,
+               "crossings_per_launch": cross / args.launches, "scat_per_s": scat / args.launches / ms * 1e3}
+    elif args.profile_case == "emissivity":
+        # the rich walk filling the envelope's emissivity cube (3 cameras)
+        p = W.envelope(n=args.grid, n_ch=args.channels, n_packets=args.packets)
+        g = krl.Grid(p)
+        try:
+            g.run(n=args.packets // 10, first=1 << 40, want_stats=False)
+            g.reset()
+
+            def one():
+                k[0] += 1
+                g.run(n=args.packets, first=k[0] * args.packets, want_stats=False)
+            ms = _timed_launches(one, args.launches)
+            st = g.tally("stats").cpu().numpy()
+        finally:
+            g.close()
+        scat, cross = int(st[4]), int(st[5])
+        out = {"case": "emissivity", "grid": args.grid, "channels": args.channels, "packets": args.packets,
+               "ms_per_launch": ms, "segments_per_s": (scat + cross) / args.launches / ms * 1e3,
+               "packets_per_s": args.packets / ms * 1e3}
+    else:
+        p = W.envelope(n=args.grid, n_ch=args.channels, n_packets=200_000)
+        g = krl.Grid(p)
+        try:
+            g.run(want_stats=False)
+            g.raytrace(0, args.pixels, args.pixels, fov_cells=float(args.grid))
+            ms = _timed_launches(lambda: g.raytrace(1, args.pixels, args.pixels, fov_cells=float(args.grid)),
+                                 args.launches)
+        finally:
+            g.close()
+        rays = args.pixels * args.pixels
+        out = {"case": "raytrace", "grid": args.grid, "pixels": args.pixels, "channels": args.channels,
+               "ms_per_launch": ms, "rays_per_s": rays / ms * 1e3}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, rank):
     """The FP64 oracle as it stands, on the host cores, a bounded sample per step."""
     if rank != 0:
@@ -443,6 +537,13 @@ def cpu_baseline(p):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile_case:
+        args.packets = 1 << 21 if args.packets is None else args.packets
+        args.tau0 = 3e4 if args.tau0 is None else args.tau0
+        profile_case(args)
+        return
+    args.packets = PACKETS_PER_STEP if args.packets is None else args.packets
+    args.tau0 = 1e6 if args.tau0 is None else args.tau0
     if args.impl == "reference":
         if world > 1:
             import torch.distributed as dist
@@ -549,6 +650,25 @@ def main():
                            f"{sm_max:.0f} MHz ({peak_kind} max SM clock)",
             "ops_per_scattering": OPS_PER_SCAT, "ops_per_crossing": OPS_PER_CROSS}
 
+    # One more job alone on one stream (no overlap of its tail with another
+    # job): the rate a single job gets, beside the streamed rate above.
+    serial = None
+    if not args.no_serial_leg and world == 1 and nstr > 1:
+        lo, n = shard.step_range(step_id, rank, world, B)
+        step_id += 1
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s0.record(stream)
+        g.run(n=n, first=lo, want_stats=False, stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        st_after = g.tally("stats").cpu().numpy()
+        sec = s0.elapsed_time(s1) / 1e3
+        js = int(st_after[4]) - scat
+        serial = {"scatterings_per_s": js / sec, "s": sec, "packets": n, "scatterings": js,
+                  "alu_frac": (OPS_PER_SCAT * js + OPS_PER_CROSS * (int(st_after[5]) - cross)) / sec / peak_ops}
+
     # End to end through the public API with host buffers, jobs streamed the
     # way a user runs several: each job's grid is created from pinned host
     # fields on one of two alternating streams, its run and its result reads
@@ -622,7 +742,7 @@ def main():
                        "parallelism": f"packet-id shards x{world}",
                        "exchange": f"tally all-reduce, {exchange_bytes} bytes per rank" if world > 1 else "none"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "raytrace": rt, "batch": bt,
-            "next_rows": nx, "crossings_per_s": cross_all / t_max,
+            "next_rows": nx, "crossings_per_s": cross_all / t_max, "one_stream_job": serial,
             "gpu_launches": 2 * args.steps, "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

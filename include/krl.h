@@ -199,8 +199,10 @@ typedef struct {
     int ctas_per_sm;            /* resident CTAs per SM of the persistent grid      */
     int refill_min;             /* a warp takes new packets once at least this many
                                    of its lanes are idle (1..32)                    */
-    uint64_t max_iters;         /* per-packet cap on walk iterations (budget); values
-                                   above 2^32 - 1 act as 2^32 - 1                   */
+    uint64_t max_iters;         /* per-packet cap on walk iterations (budget);
+                                   0: 2^32 - 1 (the default); larger values are
+                                   rejected with KRL_ERR_ARG (the walk counts a
+                                   packet's events in 32 bits)                      */
     int64_t emiss_records;      /* FP32 runs with an emissivity tally deposit it in
                                    two stages: the walk records each segment (32 B)
                                    in a stream-ordered buffer of this many records,
@@ -238,9 +240,14 @@ typedef struct {
  * records[id - first_id]. stats (host, may be NULL): when given, the call
  * synchronises `s` and returns this run's counters, and returns
  * KRL_ERR_BUDGET if any packet exhausted max_iters. n = 0 is a no-op.
- * Up to 8 runs of one grid may be in flight at once on different streams
- * (each takes the next of 8 scratch slots in turn); tallies accumulate
- * atomically, so their order does not matter beyond FP64 rounding.
+ * Runs of one grid may be in flight at once on different streams and be
+ * issued from several host threads: each takes the next of 8 scratch slots
+ * in turn, and a run that reuses a slot first waits, on its own stream, for
+ * the slot's previous run to finish with it (an event recorded after that
+ * run's last read of the slot); tallies accumulate atomically, so their
+ * order does not matter beyond FP64 rounding. A run enqueued while `s` is
+ * being captured into a CUDA graph keeps its slot inside the graph without
+ * that wait: replays of such a graph must not overlap other runs of the grid.
  * An FP32 run of a line with an emissivity tally also allocates and frees
  * its segment buffer in stream order on `s` (cudaMallocAsync / cudaFreeAsync,
  * size set by krl_tune.emiss_records), so the call stays capturable in a
@@ -364,8 +371,10 @@ KRL_API krl_status krl_batch_destroy(krl_batch* b);
  * (tune->block; KRL_ERR_ARG above). Each packet's
  * random stream, and therefore every tally, is exactly what krl_run_packets
  * on that grid with the same (seed, ids) gives. Tallies accumulate into each
- * grid. stats (host [n_models] or NULL): per-model counters; when given the
- * call synchronises `s`. The call first waits for `s` (it rewrites a pinned
+ * grid. records (host [n_models] of device pointers, or NULL; a NULL entry
+ * skips that model): model m's packet records, records[m][id - first_ids[m]],
+ * as krl_run_packets writes them. stats (host [n_models] or NULL): per-model
+ * counters; when given the call synchronises `s`. The call first waits for `s` (it rewrites a pinned
  * argument mirror the previous run's copy reads), then enqueues a copy of
  * the arguments, the launch and the counter updates; captured into a CUDA
  * graph (stats must then be NULL, and the stream must be idle when the
@@ -373,7 +382,8 @@ KRL_API krl_status krl_batch_destroy(krl_batch* b);
  * again and reruns the same packets.
  */
 KRL_API krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* first_ids, uint64_t seed,
-                                 const krl_tune* tune, krl_run_stats* stats, krl_stream s);
+                                 const krl_tune* tune, krl_packet_record* const* records, krl_run_stats* stats,
+                                 krl_stream s);
 
 /* ------------------------------------------------------------------ channel maps */
 

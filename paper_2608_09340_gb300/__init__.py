@@ -153,7 +153,7 @@ def load_library(path: str | None = None):
                                        C.POINTER(C.c_double), vp]
     lib.krl_batch_destroy.argtypes = [vp]
     lib.krl_batch_run.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_uint64,
-                                  C.POINTER(krl_tune), C.POINTER(krl_run_stats), vp]
+                                  C.POINTER(krl_tune), C.POINTER(vp), C.POINTER(krl_run_stats), vp]
     for name in ("krl_grid_create", "krl_grid_destroy", "krl_line_set", "krl_line_info_get",
                  "krl_run_packets", "krl_tallies_get", "krl_tallies_reset", "krl_emission_cdf_noalloc",
                  "krl_raytrace_channels", "krl_batch_create", "krl_batch_destroy", "krl_batch_run",
@@ -390,14 +390,23 @@ class Batch:
         self.handle = h
 
     def run(self, packets, first_ids=None, seed: int = 0, precision: int = KRL_PREC_FP32, block: int = 0,
-            ctas_per_sm: int = 0, refill_min: int = 0, max_iters: int = 0, want_stats: bool = False, stream=None):
+            ctas_per_sm: int = 0, refill_min: int = 0, max_iters: int = 0, want_stats: bool = False, stream=None,
+            records=None):
+        """records: None, or one device tensor (or None) per model that
+        receives that model's packet records (RECORD_DTYPE, one per packet)."""
         n = len(self.grids)
         pk = (C.c_uint64 * n)(*[int(v) for v in packets])
         fi = (C.c_uint64 * n)(*[int(v) for v in first_ids]) if first_ids is not None else None
         tune = krl_tune(precision, block, ctas_per_sm, refill_min, max_iters)
         st = (krl_run_stats * n)() if want_stats else None
+        rp = None
+        if records is not None:
+            for r, k in zip(records, packets):
+                if r is not None and r.numel() * r.element_size() < int(k) * RECORD_DTYPE.itemsize:
+                    raise ValueError("record buffer smaller than the model's packet count")
+            rp = (C.c_void_p * n)(*[None if r is None else r.data_ptr() for r in records])
         rc = load_library().krl_batch_run(self.handle, pk, fi, int(seed) & ((1 << 64) - 1), C.byref(tune),
-                                          st, _stream_handle(stream))
+                                          rp, st, _stream_handle(stream))
         if not (rc == KRL_ERR_BUDGET and st is not None):
             _check(rc)
         return (list(st) if st is not None else None), rc

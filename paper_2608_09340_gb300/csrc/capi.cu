@@ -8,6 +8,8 @@
 
 #include <new>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "krl_internal.cuh"
@@ -52,7 +54,12 @@ struct krl_grid {
     // be in flight together (each slot: work counter + ST_N run counters)
     unsigned long long* run_stats = nullptr;  // [kSlots][ST_N]
     unsigned long long* next = nullptr;       // [kSlots] work counters
-    unsigned run_seq = 0;
+    std::atomic<unsigned> run_seq{0};         // runs take slots round robin
+    // A slot is reused by every 8th run: the next user waits (on its own
+    // stream) for the event recorded after the previous user's last read of
+    // the slot; the slot's mutex orders that wait and record on the host.
+    cudaEvent_t slot_ev[8] = {};
+    std::mutex slot_mu[8];
     int* bad = nullptr;                       // validation flags
     double* scan_work = nullptr;
     size_t scan_work_n = 0;
@@ -272,7 +279,7 @@ void fill_args(const krl_grid* g, TransportArgs& A, uint64_t n, uint64_t first_i
     A.k1 = (unsigned)(seed >> 32);
     A.keys = round_keys(seed);
     A.max_iters = T.max_iters;
-    A.max_iters32 = T.max_iters > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned)T.max_iters;
+    A.max_iters32 = (unsigned)T.max_iters;        // resolve_tune keeps it below 2^32
     A.refill_min = T.refill_min;
     A.tau_abs = g->tau_abs;
     A.absw = g->absw;
@@ -305,7 +312,7 @@ bool blend_crossing(double a, double* u0)
 
 krl_status resolve_tune(const krl_tune* tune, krl_tune& T)
 {
-    T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 1ull << 40, 0};
+    T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 0xFFFFFFFFull, 0};
     if (tune) {
         if (tune->emiss_records < -1 || tune->emiss_records > (1ll << 36))
             return fail(KRL_ERR_ARG, "emiss_records must be in [-1, 2^36]");
@@ -316,6 +323,8 @@ krl_status resolve_tune(const krl_tune* tune, krl_tune& T)
         if (tune->block) T.block = tune->block;
         if (tune->ctas_per_sm) T.ctas_per_sm = tune->ctas_per_sm;
         if (tune->refill_min) T.refill_min = tune->refill_min;
+        if (tune->max_iters > 0xFFFFFFFFull)
+            return fail(KRL_ERR_ARG, "max_iters must be at most 2^32 - 1 (the walk counts events in 32 bits)");
         if (tune->max_iters) T.max_iters = tune->max_iters;
     }
     if (T.block && (T.block < 32 || T.block > 512 || T.block % 32))
@@ -338,7 +347,7 @@ extern "C" {
 
 const char* krl_last_error(void) { return g_err; }
 
-int krl_version(void) { return 300; }       // 0.3.0: krl_tune.emiss_records (two-stage deposit)
+int krl_version(void) { return 400; }       // 0.4.0: krl_batch_run takes per-model record buffers
 
 krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st)
 {
@@ -379,6 +388,7 @@ krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st
     if (e == cudaSuccess) e = dalloc(&g->run_stats, (size_t)kSlots * ST_N);
     if (e == cudaSuccess) e = dalloc(&g->next, (size_t)kSlots);
     if (e == cudaSuccess) e = dalloc(&g->bad, 1);
+    for (int k = 0; k < kSlots && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&g->slot_ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->bad, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->opacity, d->opacity, n * 4, cudaMemcpyDeviceToDevice, s);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
@@ -428,6 +438,8 @@ krl_status krl_grid_destroy(krl_grid* g)
     dfree(g->run_stats);
     dfree(g->next);
     dfree(g->bad);
+    for (int k = 0; k < kSlots; ++k)
+        if (g->slot_ev[k]) cudaEventDestroy(g->slot_ev[k]);
     delete g;
     return KRL_OK;
 }
@@ -605,11 +617,18 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
 
     TransportArgs A{};
     fill_args(g, A, n, first_id, seed, T, records);
-    const int slot = (int)(g->run_seq++ % kSlots);
+    const int slot = (int)(g->run_seq.fetch_add(1u, std::memory_order_relaxed) % kSlots);
     unsigned long long* slot_stats = g->run_stats + (size_t)slot * ST_N;
     unsigned long long* slot_next = g->next + slot;
     A.stats = slot_stats;
     A.next = slot_next;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    KRL_CUDA(cudaStreamIsCapturing(s, &cap), "krl_run_packets");
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    std::lock_guard<std::mutex> slot_lock(g->slot_mu[slot]);
+    // the slot's previous user must have read its counters before they are
+    // reset here (eager calls; a captured run keeps its slot in the graph)
+    if (!capturing) KRL_CUDA(cudaStreamWaitEvent(s, g->slot_ev[slot], 0), "wait for the slot's previous run");
 
     KRL_CUDA(cudaMemsetAsync(slot_next, 0, sizeof(unsigned long long), s), "reset work counter");
     KRL_CUDA(cudaMemsetAsync(slot_stats, 0, ST_N * sizeof(unsigned long long), s), "reset run counters");
@@ -639,9 +658,10 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     }
     if (le != cudaSuccess) return cuda_fail(le, "transport launch");
     KRL_CUDA(add_counters(g->stats, slot_stats, ST_N, s), "accumulate counters");
+    unsigned long long h[ST_N];
+    if (stats) KRL_CUDA(cudaMemcpyAsync(h, slot_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "read counters");
+    if (!capturing) KRL_CUDA(cudaEventRecord(g->slot_ev[slot], s), "release the run's slot");
     if (stats) {
-        unsigned long long h[ST_N];
-        KRL_CUDA(cudaMemcpyAsync(h, slot_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "read counters");
         KRL_CUDA(cudaStreamSynchronize(s), "krl_run_packets");
         stats->emitted = h[ST_EMITTED];
         stats->escaped = h[ST_ESCAPED];
@@ -805,7 +825,8 @@ krl_status krl_batch_create(krl_batch** out, krl_grid* const* grids, int n_model
 }
 
 krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* first_ids, uint64_t seed,
-                         const krl_tune* tune, krl_run_stats* stats, krl_stream st)
+                         const krl_tune* tune, krl_packet_record* const* records, krl_run_stats* stats,
+                         krl_stream st)
 {
     cudaStream_t s = (cudaStream_t)st;
     if (!b || !packets) return fail(KRL_ERR_ARG, "krl_batch_run: NULL argument");
@@ -841,7 +862,7 @@ krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* 
         const int m = order[k];
         TransportArgs& A = b->h_args[k];
         A = TransportArgs{};
-        fill_args(b->grids[m], A, packets[m], first_ids ? first_ids[m] : 0, seed, T, nullptr);
+        fill_args(b->grids[m], A, packets[m], first_ids ? first_ids[m] : 0, seed, T, records ? records[m] : nullptr);
         A.next = b->d_counts + m;
         A.stats = b->d_counts + n + (size_t)m * ST_N;
     }

@@ -40,13 +40,23 @@ constexpr size_t kRquadElems = (size_t)(kRnG - 1) * (kRnX - 1) * kRnD;
 constexpr int kGuideN = 256;
 constexpr double kGuideW = 16.7;
 
+// Row guide of the sampler: bins of |x| by the top bits of its float32
+// encoding (exponent and 4 mantissa bits: 16 bins per octave) from 0.25 up
+// to 512; entry t is the largest row i <= kUsNx - 2 whose node x_i is <= the
+// bin's lower edge. Every bin holds at most one node (the rows are 4/9 apart
+// below |x| = 8 and a factor 1.19 apart above; a CPU test checks the node
+// set), so the row of any |x| is the entry or the one after it.
+constexpr int kRowGuideN = 176;
+constexpr unsigned kRowGuideBase = 0x3E800000u >> 19;   // float32 bits of 0.25, >> 19
+
 // Shared-memory image of the per-line sampling tables used by the walk.
 constexpr int kSmemVoigt = 0;
 constexpr int kSmemUsX = kVoigtN;                 // 40 floats
 constexpr int kSmemUsC = kVoigtN + 48;            // 40 x 251 floats
 constexpr int kSmemFloats = kSmemUsC + kUsNx * kUsNu;
 constexpr int kSmemGuideBytes = kUsNx * kGuideN;  // uint8 after the floats
-constexpr size_t kSmemBytes = (size_t)kSmemFloats * sizeof(float) + kSmemGuideBytes;
+constexpr int kSmemRowGuide = kSmemFloats * (int)sizeof(float) + kSmemGuideBytes;   // byte offset
+constexpr size_t kSmemBytes = (size_t)kSmemRowGuide + 192;
 
 // ---------------------------------------------------------------- compile-time walk features
 enum : unsigned {

@@ -25,14 +25,10 @@ cudaError_t launch_emiss_deposit(const TransportArgs& A, unsigned features, int 
 {
     const bool vel = (features & F_VEL) != 0;
     auto kern = vel ? k_emiss_deposit<true> : k_emiss_deposit<false>;
-    static int occ[2] = {0, 0};      // resident CTAs per SM, per instantiation
-    if (!occ[vel]) {
-        int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kDepositBlock, 0);
-        if (e != cudaSuccess) return e;
-        occ[vel] = o > 0 ? o : 1;
-    }
-    kern<<<sm_count * occ[vel], kDepositBlock, 0, s>>>(A);
+    int occ = 0;                     // resident CTAs per SM on the current device
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDepositBlock, 0);
+    if (e != cudaSuccess) return e;
+    kern<<<sm_count * (occ > 0 ? occ : 1), kDepositBlock, 0, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -133,9 +133,10 @@ struct Ops<double> {
 
 // ---------------------------------------------------------------- table lookups (shared memory)
 
-// H(a, x) from the ph_mode 2 slice: ln H linear in log10|x| between nodes.
-// The three ranges are evaluated without branches and the result selected
-// (every path is finite or discarded for any x).
+// H(a, x) from the ph_mode 2 slice: ln H linear in log10|x| between nodes;
+// H(a, 0) below |x| = 1e-4 and the wing series above 1e3. The table path is
+// evaluated for every x (finite for any x); the two outer ranges, which a
+// walk rarely reaches, replace it in a branch of their own.
 template <typename R>
 __device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
 {
@@ -146,16 +147,19 @@ __device__ __forceinline__ R voigt(R x, const float* sv, R a, R H0)
     i = i < 0 ? 0 : (i > kVoigtN - 2 ? kVoigtN - 2 : i);
     const R f = t - (R)i;
     const R l0 = (R)sv[i], l1 = (R)sv[i + 1];
-    const R tab = O::ex(((R)1 - f) * l0 + f * l1);
-    const R ax2 = ax * ax;
-    R wing;
-    if constexpr (sizeof(R) == 4) {
-        const float r = Ops<float>::rcp(ax2);                     // one reciprocal: a r (1 + 3r/2) / sqrt(pi)
-        wing = (a * 0.56418958354775628f) * r * fmaf(1.5f, r, 1.0f);
-    } else {
-        wing = a / ((R)1.7724538509055160 * ax2) * ((R)1 + (R)1.5 / ax2);
+    R h = O::ex(((R)1 - f) * l0 + f * l1);
+    if (ax < (R)1e-4 || ax > (R)1e3) {
+        const R ax2 = ax * ax;
+        R wing;
+        if constexpr (sizeof(R) == 4) {
+            const float r = Ops<float>::rcp(ax2);                 // one reciprocal: a r (1 + 3r/2) / sqrt(pi)
+            wing = (a * 0.56418958354775628f) * r * fmaf(1.5f, r, 1.0f);
+        } else {
+            wing = a / ((R)1.7724538509055160 * ax2) * ((R)1 + (R)1.5 / ax2);
+        }
+        h = ax < (R)1e-4 ? H0 : wing;
     }
-    return ax < (R)1e-4 ? H0 : (ax > (R)1e3 ? wing : tab);
+    return h;
 }
 
 // Line-profile mode 1: ln H bilinear in (log10 a, log10|x|) on the global
@@ -210,28 +214,25 @@ __device__ __forceinline__ R profile(const TransportArgs& A, R x, const float* s
     else return voigt<R>(x, sv, a, H0);
 }
 
-// Largest row i in [0, 38] with X[i] <= ax: closed-form guess from the node
-// formula, then one fix-up against the stored nodes (the guess is off by at
-// most one). Returns i and the two bracketing nodes.
+// Largest row i in [0, 38] with X[i] <= ax, and the two bracketing nodes:
+// the row guide's entry for the bin of ax (a node at or below ax), then one
+// step up if the next node is also <= ax. The FP64 walk takes the bin of ax
+// rounded toward zero, so the entry stays at or below ax there too.
 template <typename R>
-__device__ __forceinline__ int us_row2(R ax, const float* sx, R& x0, R& x1)
+__device__ __forceinline__ int us_row2(R ax, const float* sx, const unsigned char* rg, R& x0, R& x1)
 {
-    // both guesses without a branch (the log one is finite for ax >= 0)
-    const int ilin = (int)(ax * (R)2.25);
-    const int ilog = 18 + (int)((R)21 * Ops<R>::ln(ax * (R)0.125) * (R)0.27588297880498553);  // 1/ln(37.5)
-    int i = ax < (R)8 ? ilin : ilog;
-    i = i < 0 ? 0 : (i > kUsNx - 2 ? kUsNx - 2 : i);
-    // The guess is off by at most one row (rounding of ax 2.25 next to a node,
-    // or the log's error next to a node): the four nodes around it are read
-    // together and the bracket is selected without a branch.
+    float f;
+    if constexpr (sizeof(R) == 4) f = ax;
+    else f = __double2float_rz(ax);
+    int t = (int)(__float_as_uint(f) >> 19) - (int)kRowGuideBase;
+    t = t < 0 ? 0 : (t > kRowGuideN - 1 ? kRowGuideN - 1 : t);
+    const int i = rg[t];
     const R g0 = (R)sx[i], g1 = (R)sx[i + 1];
-    const R gm = (R)sx[i > 0 ? i - 1 : 0];
     const R gp = (R)sx[i < kUsNx - 2 ? i + 2 : kUsNx - 1];
-    const bool dn = i > 0 && g0 > ax;
     const bool up = i < kUsNx - 2 && g1 <= ax;
-    x0 = dn ? gm : (up ? g1 : g0);
-    x1 = dn ? g0 : (up ? gp : g1);
-    return i - (dn ? 1 : 0) + (up ? 1 : 0);
+    x0 = up ? g1 : g0;
+    x1 = up ? gp : g1;
+    return i + (up ? 1 : 0);
 }
 
 // u_par for incoming gas-frame frequency x (|x| <= 300), given L = ln(xi)
@@ -241,12 +242,13 @@ __device__ __forceinline__ int us_row2(R ax, const float* sx, R& x0, R& x1)
 // linear between nodes j and j + 1; the two rows' u are interpolated in |x|.
 // The two rows are walked together so their shared-memory loads overlap.
 template <typename R>
-__device__ __forceinline__ R us_sample(R x, R L, int m, const float* sx, const float* sc, const unsigned char* sg)
+__device__ __forceinline__ R us_sample(R x, R L, int m, const float* sx, const float* sc, const unsigned char* sg,
+                                       const unsigned char* rg)
 {
     using O = Ops<R>;
     const R ax = fabs(x);
     R x0, x1;
-    const int i = us_row2(ax, sx, x0, x1);
+    const int i = us_row2(ax, sx, rg, x0, x1);
     const R t = O::dv(ax - x0, x1 - x0);
     const float* ra = sc + i * kUsNu;
     const float* rb = ra + kUsNu;
@@ -756,6 +758,9 @@ constexpr int kCtlInts = 4 + 2 * 32;
 constexpr size_t kStashOff = kCtlOff + (size_t)kCtlInts * sizeof(int);
 // Events a lane runs between two compaction checks in the tail.
 constexpr int kTailRound = 32;
+// Bulk-phase iterations between two reads of the CTA's stop flag by a warp
+// with no idle lane.
+constexpr int kBulkCheck = 16;
 
 // Words per stashed packet: cell (c, cx, cy, cz), nscat, ncross, cell0, id
 // (2 words), and px, py, pz, nx, ny, nz, x, tau (and the weight in the rich
@@ -869,8 +874,8 @@ __device__ __forceinline__ R seg_factor(R dt, R& ab)
 // packet has ended (escape, destruction or event budget).
 template <typename R, unsigned F, int PH>
 __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p, const float* sv,
-                                        const float* sx,
-                                        const float* sc, const unsigned char* sg, R a, R H0, LaneStats& st)
+                                        const float* sx, const float* sc, const unsigned char* sg,
+                                        const unsigned char* rg, R a, R H0, LaneStats& st)
 {
     using O = Ops<R>;
     if (p.nscat + p.ncross >= A.max_iters32) {
@@ -961,7 +966,7 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
         const int gm = us_bin<R>(O::uni(w0.w[0]), L);
         const R tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
         const R z1 = rad * bc, z2 = rad * bs;
-        const R us = us_sample<R>(xcom, L, gm, sx, sc, sg);   // finite for any x; unused beyond 300
+        const R us = us_sample<R>(xcom, L, gm, sx, sc, sg, rg);   // finite for any x; unused beyond 300
         const R upar = fabs(xcom) > (R)300 ? z2 : us;
         const R g = p.nx * mx + p.ny * my + p.nz * mz;
         const R sg_ = O::sq(fmax((R)0, (R)1 - g * g));
@@ -1047,6 +1052,16 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
     const float* sx = PH == 1 ? A.us_x : sm + kSmemUsX;
     const float* sc = PH == 1 ? A.us_lncdf : sm + kSmemUsC;
     const unsigned char* sg = PH == 1 ? A.us_guide : sgw;
+    // the sampler's row guide, from the staged nodes (all profile modes)
+    unsigned char* rgw = reinterpret_cast<unsigned char*>(sm) + kSmemRowGuide;
+    for (int t = threadIdx.x; t < kRowGuideN; t += blockDim.x) {
+        const float edge = __uint_as_float((unsigned)(t + (int)kRowGuideBase) << 19);
+        int i = 0;
+        while (i < kUsNx - 2 && sx[i + 1] <= edge) ++i;
+        rgw[t] = (unsigned char)i;
+    }
+    __syncthreads();
+    const unsigned char* rg = rgw;
 
     const R a = (R)A.a;
     const R H0 = (R)__ldg(A.H0);
@@ -1060,15 +1075,17 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
     // Both phases run in one loop so that the event code is inlined once.
     const int n = (int)blockDim.x;
     bool bulk = true;
-    int round = 0, it = 0;
+    int round = 0, it = 0, quiet = 0;
     for (;;) {
-        if (bulk) {
-            // ---- bulk phase: refill idle lanes, leave when the ids run out
-            const unsigned idle = __ballot_sync(kFull, !active);
+        // ---- bulk phase: refill idle lanes, leave when the ids run out. A
+        // warp whose lanes are all busy skips this bookkeeping, except every
+        // kBulkCheck-th iteration, when it looks at the CTA's stop flag (the
+        // other warps may be waiting for it at the tail barrier).
+        const unsigned idle = bulk ? __ballot_sync(kFull, !active) : 0u;
+        if (bulk && (idle != 0u || ++quiet == kBulkCheck)) {
+            quiet = 0;
             const int nidle = __popc(idle);
-            int stop = 0;
-            if (lane == 0) stop = *reinterpret_cast<volatile int*>(ctl);
-            bool leave = __shfl_sync(kFull, stop, 0) != 0;
+            bool leave = *reinterpret_cast<volatile int*>(ctl) != 0;   // one broadcast read
             if (!leave && (nidle == 32 || (nidle > 0 && nidle >= A.refill_min))) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(A.next, (unsigned long long)nidle);
@@ -1094,7 +1111,7 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
                 bulk = false;
                 __syncthreads();
             }
-        } else if (it == kTailRound || !__any_sync(kFull, active)) {
+        } else if (!bulk && (it == kTailRound || !__any_sync(kFull, active))) {
             // ---- tail phase, end of a round: count and compact
             const unsigned m = __ballot_sync(kFull, active);
             int* cnt = ctl + 4 + 32 * (round & 1);
@@ -1123,7 +1140,7 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
             it = 0;
         }
         if (!bulk) ++it;
-        if (active) active = advance<R, F, PH>(A, K, p, sv, sx, sc, sg, a, H0, st);
+        if (active) active = advance<R, F, PH>(A, K, p, sv, sx, sc, sg, rg, a, H0, st);
     }
 
     const unsigned long long tot[7] = {warp_sum(st.emit),  warp_sum(st.esc),  warp_sum(st.des),
@@ -1195,13 +1212,12 @@ cudaError_t launch_one(const TransportArgs& A, int grid, int block, cudaStream_t
 {
     if (block > max_block<R, F>()) return cudaErrorInvalidConfiguration;
     auto kern = k_transport<R, F, PH>;
-    static bool configured = false;   // per instantiation, per process
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes<R, F>(max_block<R, F>()));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // the shared-memory opt-in is an attribute of the kernel on the current
+    // device: set it on every launch (a host-side call of about a
+    // microsecond), so that a launch on any device of the process has it
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<R, F>(max_block<R, F>()));
+    if (e != cudaSuccess) return e;
     kern<<<grid, block, smem_bytes<R, F>(block), s>>>(A);
     return cudaGetLastError();
 }
@@ -1211,13 +1227,9 @@ cudaError_t launch_batch_one(const BatchArgs& B, int grid, int block, cudaStream
 {
     if (block > kBatchBlock) return cudaErrorInvalidConfiguration;
     auto kern = k_transport_batch<R, F>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes<R, F>(kBatchBlock));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<R, F>(kBatchBlock));   // per device: every launch
+    if (e != cudaSuccess) return e;
     kern<<<grid, block, smem_bytes<R, F>(block), s>>>(B);
     return cudaGetLastError();
 }

@@ -1,4 +1,6 @@
-"""Many models in one persistent launch (krl_batch_run) give exactly the
+"""Many models in one persistent launch (krl_batch_run, the server-worker
+scheduling of Sec. 2.3.2 over models): against the oracle model by model
+(FP64 lockstep, and one FP32 model against a stored oracle run), exactly the
 tallies of one krl_run_packets launch per model (one of them with continuum
 absorption), also when the batched launch is captured into a CUDA graph and
 replayed."""
@@ -6,7 +8,8 @@ import numpy as np
 import pytest
 
 import workloads as W
-from _gpu_common import need_gpu
+import _oracle_stats as S
+from _gpu_common import check_lockstep, chi2_two_sample, grid_tallies, need_gpu, rel_l1, report
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +65,73 @@ def test_batch_equals_one_launch_per_model():
     finally:
         for g in grids:
             g.close()
+
+
+def test_batch_fp64_against_the_oracle():
+    """The batched kernel in FP64 (the same walk in double): every model's
+    packet records agree with the oracle's for >= 99.9 % of the packets, and
+    its tallies and counters element by element (packets that diverge are
+    rerun alone on both sides and taken out)."""
+    krl = need_gpu()
+    import torch
+    ms = _models()
+    grids = [krl.Grid(p) for p in ms]
+    try:
+        b = krl.Batch(grids)
+        recs = [torch.empty(p.n_packets * krl.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda") for p in ms]
+        st, rc = b.run([p.n_packets for p in ms], first_ids=[100] * len(ms), seed=11, precision=krl.KRL_PREC_FP64,
+                       records=recs, want_stats=True)
+        torch.cuda.synchronize()
+        for m, (p, g) in enumerate(zip(ms, grids)):
+            gpu = grid_tallies(g)
+            gpu["records"] = krl.records_to_numpy(recs[m])
+            assert st[m].emitted == p.n_packets
+            ok, _ = check_lockstep(krl, p, gpu, p.n_packets, first=100, seed=11, label=f"batched model {m}")
+            report("batch_fp64_lockstep", model=m, name=p.name, packets=p.n_packets, identical=float(ok.mean()))
+        b.close()
+    finally:
+        for g in grids:
+            g.close()
+
+
+def test_batch_fp32_model_against_the_oracle():
+    """One model of an FP32 batch -- the 32^3, tau0 = 1e5 outflow sphere at
+    6e5 packets, batched with three other models -- against the stored FP64
+    oracle run on the same ids and seed: relative L1 < 2 % and chi^2 p > 0.01
+    of the escaped spectrum, and the scattering map's radial profile."""
+    krl = need_gpu()
+    import torch
+    run = S.load("sphere32_tau1e5_out200_n6e5_seed0")
+    assert S.is_current(run)
+    seed = run["seed"]
+    target = W.sphere(**run["workload"]["kwargs"], seed=seed)
+    others = [W.sphere(vmax_kms=-150.0, tau0=3e4, n=24, n_packets=200_000, seed=seed),
+              W.slab(tau0=1e4, n_packets=100_000, seed=seed),
+              W.sphere(vmax_kms=0.0, tau0=1e4, n=48, n_packets=50_000, a=1e-3, seed=seed)]
+    ms = [others[0], target] + others[1:]
+    grids = [krl.Grid(p) for p in ms]
+    try:
+        b = krl.Batch(grids)
+        pk = [p.n_packets for p in ms]
+        pk[1] = run["n"]
+        b.run(pk, first_ids=[run["first"]] * len(ms), seed=seed)
+        torch.cuda.synchronize()
+        t = grid_tallies(grids[1])
+        b.close()
+    finally:
+        for g in grids:
+            g.close()
+    g_ = t["spec_n"].astype(np.int64)
+    r = np.asarray(run["spec_c"], dtype=np.int64)
+    l1, pv = rel_l1(g_, r), chi2_two_sample(g_, r)[2]
+    gs = S.shell_profile(t["scatmap"], target.shape)
+    rs = np.asarray(run["shells_per_batch"], dtype=np.float64).sum(axis=0)
+    z = S.shell_z(gs, run["n"], run)
+    report("batch_fp32_vs_oracle", case=run["case"], spectrum_l1=l1, spectrum_chi2_p=pv,
+           shell_l1=rel_l1(gs, rs), shell_max_abs_z=float(np.abs(z).max()))
+    assert int(g_.sum()) == run["n"]
+    assert l1 < 0.02 and pv > 0.01, (l1, pv)
+    assert rel_l1(gs, rs) < 0.02 and np.abs(z).max() < 4.5, z
 
 
 def test_batch_in_a_cuda_graph():

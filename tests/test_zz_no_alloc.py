@@ -56,7 +56,10 @@ def test_noalloc_cdf_matches_the_allocating_path_on_two_calls():
     big = rng.gamma(2.0, 1.0, size=(40, 40, 40)).astype(np.float32)
     big[big < 0.3] = 0.0                                   # some empty cells
     small = rng.uniform(0.0, 5.0, size=(17, 19, 23)).astype(np.float32)   # ragged, < 1 scan block per row
-    for rate in (big, small):                              # the second call reuses the first's scratch
+    # 2,080,000 cells: 1016 scan blocks of 2048 cells, the last one ragged, so
+    # that each thread of the block-offset pass sums several block totals
+    huge = rng.exponential(1.0, size=(130, 125, 128)).astype(np.float32)
+    for rate in (big, small, huge):                        # later calls reuse the earlier calls' scratch
         ref = _reference_cdf(krl, rate)
         r = torch.from_numpy(rate.reshape(-1)).cuda()
         out = torch.full((rate.size,), float("nan"), dtype=torch.float64, device="cuda")
@@ -65,6 +68,10 @@ def test_noalloc_cdf_matches_the_allocating_path_on_two_calls():
         got = out.cpu().numpy()
         assert np.allclose(got, ref, rtol=1e-13, atol=1e-15)
         assert got[-1] == 1.0 and np.all(np.diff(got) >= 0)
+        # and against the definition itself: the FP64 running sum of the rates
+        # over their total (numpy, independent of both device paths)
+        cs = np.cumsum(rate.reshape(-1).astype(np.float64))
+        assert np.allclose(got, cs / cs[-1], rtol=1e-12, atol=1e-15)
 
 
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
