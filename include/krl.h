@@ -225,6 +225,10 @@ typedef struct {
                                    4 absorbed (weight below the cut)                */
     uint16_t pad;
     uint32_t cell0;             /* flat index of the emission cell                 */
+    uint32_t scat_cells;        /* FP64 walk: sum over the packet's scatterings of
+                                   the flat index of the cell it scattered in
+                                   (mod 2^32), a check that two walks scattered in
+                                   the same cells; 0 from the FP32 walk            */
 } krl_packet_record;
 
 typedef struct {

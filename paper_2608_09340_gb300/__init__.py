@@ -111,8 +111,8 @@ class krl_run_stats(C.Structure):
 
 
 RECORD_DTYPE = np.dtype([("x", "<f4"), ("nscat", "<u4"), ("ncross", "<u4"), ("status", "<u2"),
-                         ("pad", "<u2"), ("cell0", "<u4")])
-assert RECORD_DTYPE.itemsize == 20
+                         ("pad", "<u2"), ("cell0", "<u4"), ("scat_cells", "<u4")])
+assert RECORD_DTYPE.itemsize == 24
 
 EXPORTS = ["krl_last_error", "krl_version", "krl_grid_create", "krl_grid_destroy", "krl_line_set",
            "krl_line_info_get", "krl_run_packets", "krl_tallies_get", "krl_tally_bytes", "krl_tallies_reset",

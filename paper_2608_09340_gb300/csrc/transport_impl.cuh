@@ -256,16 +256,19 @@ __device__ __forceinline__ R us_sample(R x, R L, int m, const float* sx, const f
     int jb = sg[(i + 1) * kGuideN + m];
     R a0 = (R)ra[ja], a1 = (R)ra[ja + 1];
     R b0 = (R)rb[jb], b1 = (R)rb[jb + 1];
+    // Every row starts at the floor ln 1e-30 < L and ends at ln 1 = 0 > L
+    // (L is the log of a uniform in [2^-24, 1 - 2^-24]), so both walks stop
+    // inside the row without bound checks.
     for (;;) {
-        const bool da = ja > 0 && a0 > L;
-        const bool db = jb > 0 && b0 > L;
+        const bool da = a0 > L;
+        const bool db = b0 > L;
         if (!(da || db)) break;
         if (da) { --ja; a1 = a0; a0 = (R)ra[ja]; }
         if (db) { --jb; b1 = b0; b0 = (R)rb[jb]; }
     }
     for (;;) {
-        const bool ua = ja < kUsNu - 2 && a1 <= L;
-        const bool ub = jb < kUsNu - 2 && b1 <= L;
+        const bool ua = a1 <= L;
+        const bool ub = b1 <= L;
         if (!(ua || ub)) break;
         if (ua) { ++ja; a0 = a1; a1 = (R)ra[ja + 1]; }
         if (ub) { ++jb; b0 = b1; b1 = (R)rb[jb + 1]; }
@@ -305,6 +308,7 @@ struct Pkt {
     R wgt;                 // packet weight (continuum absorption; 1 otherwise)
     R vis_abs;             // weight absorbed by the continuum over this visit
     bool prev_scat;        // last event was a scattering (draw the next one early)
+    uint32_t cellsum;      // FP64 walk: sum of the cells of its scatterings (mod 2^32)
 };
 
 // n . V/b of a cell, always evaluated in this one fixed order (explicit
@@ -317,20 +321,16 @@ __device__ __forceinline__ R vdot(R nx, R ny, R nz, const float4& rec)
     return fma(nz, (R)rec.w, fma(ny, (R)rec.z, nx * (R)rec.y));
 }
 
+// The FP64 walk keeps 1 / n with the direction (its face distances are
+// taken every event, as the oracle takes them); the FP32 walk forms them
+// only when a packet crosses a face.
 template <typename R>
 __device__ __forceinline__ void set_dir(Pkt<R>& p, R nx, R ny, R nz)
 {
     p.nx = nx;
     p.ny = ny;
     p.nz = nz;
-    if constexpr (sizeof(R) == 4) {
-        // a zero component counts as +1e-30 (the packet then crosses that
-        // face only from exactly on it), so that 1/n is finite and its sign
-        // alone selects the face ahead
-        p.ix = Ops<R>::rcp(nx != 0.0f ? nx : 1e-30f);
-        p.iy = Ops<R>::rcp(ny != 0.0f ? ny : 1e-30f);
-        p.iz = Ops<R>::rcp(nz != 0.0f ? nz : 1e-30f);
-    } else {
+    if constexpr (sizeof(R) == 8) {
         p.ix = Ops<R>::rcp(nx);
         p.iy = Ops<R>::rcp(ny);
         p.iz = Ops<R>::rcp(nz);
@@ -385,6 +385,7 @@ __device__ __forceinline__ void write_record(const TransportArgs& A, const Pkt<R
     r.status = status;
     r.pad = 0;
     r.cell0 = p.cell0;
+    r.scat_cells = sizeof(R) == 8 ? p.cellsum : 0u;
     A.rec[p.id - A.first] = r;
 }
 
@@ -470,6 +471,7 @@ __device__ bool emit(const TransportArgs& A, const RoundKeys& K, Pkt<R>& p)
     }
     p.nscat = 0;
     p.ncross = 0;
+    p.cellsum = 0;
     p.vis_scat = 0;
     p.vis_exc = (R)0;
     p.wgt = (R)1;
@@ -720,6 +722,7 @@ __global__ void __launch_bounds__(kDepositBlock) k_emiss_deposit(const __grid_co
 template <typename R, unsigned F>
 __device__ __forceinline__ void flush_visit(const TransportArgs& A, Pkt<R>& p)
 {
+    if constexpr (sizeof(R) == 8) p.cellsum += p.vis_scat * (uint32_t)p.c;
     if ((F & F_SCAT) && p.vis_scat && A.scat) atomicAdd(A.scat + p.c, (unsigned long long)p.vis_scat);
     if ((F & F_RICH) && (A.rich & KRL_TALLY_EXC) && p.vis_exc != (R)0) atomicAdd(A.exc + p.c, (double)p.vis_exc);
     if ((F & F_RICH) && A.tau_abs && p.vis_abs != (R)0) atomicAdd(A.absw + p.c, (double)p.vis_abs);
@@ -763,10 +766,10 @@ constexpr int kTailRound = 32;
 constexpr int kBulkCheck = 16;
 
 // Words per stashed packet: cell (c, cx, cy, cz), nscat, ncross, cell0, id
-// (2 words), and px, py, pz, nx, ny, nz, x, tau (and the weight in the rich
-// walk) in R.
+// (2 words), the scattering-cell sum (FP64 walk), and px, py, pz, nx, ny, nz,
+// x, tau (and the weight in the rich walk) in R.
 template <typename R, unsigned F>
-constexpr int stash_words() { return 9 + ((F & F_RICH) ? 9 : 8) * (int)(sizeof(R) / 4); }
+constexpr int stash_words() { return 9 + (sizeof(R) == 8 ? 1 : 0) + ((F & F_RICH) ? 9 : 8) * (int)(sizeof(R) / 4); }
 
 template <typename R, unsigned F>
 constexpr size_t smem_bytes(int block) { return kStashOff + (size_t)stash_words<R, F>() * 4u * (size_t)block; }
@@ -812,6 +815,7 @@ __device__ __forceinline__ void stash_put(uint32_t* w, int n, int slot, const Pk
     w[(f++) * n + slot] = p.cell0;
     w[(f++) * n + slot] = (uint32_t)p.id;
     w[(f++) * n + slot] = (uint32_t)(p.id >> 32);
+    if constexpr (sizeof(R) == 8) w[(f++) * n + slot] = p.cellsum;
     put_r<R>(w, f, n, slot, p.px);
     put_r<R>(w, f, n, slot, p.py);
     put_r<R>(w, f, n, slot, p.pz);
@@ -837,6 +841,7 @@ __device__ __forceinline__ void stash_get(const TransportArgs& A, const uint32_t
     const uint32_t lo = w[(f++) * n + slot];
     const uint32_t hi = w[(f++) * n + slot];
     p.id = ((unsigned long long)hi << 32) | lo;
+    if constexpr (sizeof(R) == 8) p.cellsum = w[(f++) * n + slot];
     p.px = get_r<R>(w, f, n, slot);
     p.py = get_r<R>(w, f, n, slot);
     p.pz = get_r<R>(w, f, n, slot);
@@ -903,18 +908,54 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
     const R xcom = p.x - vdn;
     const R H = profile<R, PH>(A, xcom, sv, a, H0);
     const R alpha = (R)p.rec.x * H;
-    const R tx = face_dist<R>(p.px, p.nx, p.ix);
-    const R ty = face_dist<R>(p.py, p.ny, p.iy);
-    const R tz = face_dist<R>(p.pz, p.nz, p.iz);
-    R sx_ = tx;
+    bool scat;
+    R ds, sx_ = (R)0, nd = (R)0;
     int axis = 0;
-    if (ty < sx_) { sx_ = ty; axis = 1; }
-    if (tz < sx_) { sx_ = tz; axis = 2; }
-    const bool scat = p.tau < alpha * sx_;
-    const R ds = scat ? O::dv(p.tau, alpha) : sx_;
-    p.px = O::step01(p.px, ds, p.nx);
-    p.py = O::step01(p.py, ds, p.ny);
-    p.pz = O::step01(p.pz, ds, p.nz);
+    if constexpr (sizeof(R) == 4) {
+        // FP32: the packet scatters in this cell iff the point at distance
+        // tau / alpha along n lies inside the cell ([0, 1] on every axis; a
+        // line-free cell gives an infinite or NaN distance: outside). The
+        // face distances are needed only for a crossing.
+        ds = O::dv(p.tau, alpha);
+        const float qx = fmaf(ds, p.nx, p.px), qy = fmaf(ds, p.ny, p.py), qz = fmaf(ds, p.nz, p.pz);
+        scat = fabsf(qx - 0.5f) <= 0.5f && fabsf(qy - 0.5f) <= 0.5f && fabsf(qz - 0.5f) <= 0.5f;
+        if (scat) {
+            p.px = qx;
+            p.py = qy;
+            p.pz = qz;
+        } else {
+            // a zero component counts as +1e-30 (the packet then crosses that
+            // face only from exactly on it), so that 1/n is finite and its
+            // sign alone selects the face ahead
+            const float ix = O::rcp(p.nx != 0.0f ? p.nx : 1e-30f);
+            const float iy = O::rcp(p.ny != 0.0f ? p.ny : 1e-30f);
+            const float iz = O::rcp(p.nz != 0.0f ? p.nz : 1e-30f);
+            sx_ = face_dist<R>(p.px, p.nx, ix);
+            nd = ix;
+            const R ty = face_dist<R>(p.py, p.ny, iy);
+            const R tz = face_dist<R>(p.pz, p.nz, iz);
+            if (ty < sx_) { sx_ = ty; axis = 1; nd = iy; }
+            if (tz < sx_) { sx_ = tz; axis = 2; nd = iz; }
+            ds = sx_;
+            p.px = O::step01(p.px, ds, p.nx);
+            p.py = O::step01(p.py, ds, p.ny);
+            p.pz = O::step01(p.pz, ds, p.nz);
+        }
+    } else {
+        // FP64 (the lockstep walk): nearest face first, as the oracle does
+        const R tx = face_dist<R>(p.px, p.nx, p.ix);
+        const R ty = face_dist<R>(p.py, p.ny, p.iy);
+        const R tz = face_dist<R>(p.pz, p.nz, p.iz);
+        sx_ = tx;
+        nd = p.ix;
+        if (ty < sx_) { sx_ = ty; axis = 1; nd = p.iy; }
+        if (tz < sx_) { sx_ = tz; axis = 2; nd = p.iz; }
+        scat = p.tau < alpha * sx_;
+        ds = scat ? O::dv(p.tau, alpha) : sx_;
+        p.px = O::step01(p.px, ds, p.nx);
+        p.py = O::step01(p.py, ds, p.ny);
+        p.pz = O::step01(p.pz, ds, p.nz);
+    }
     if (F & F_RICH) {
         // segment tallies at the mean weight along the segment; the weight
         // then decays by the continuum's absorption over it
@@ -978,14 +1019,14 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
         return true;
     }
     // ---- cross the face on `axis`
-    p.tau -= alpha * sx_;
+    if constexpr (sizeof(R) == 4) p.tau = fmaxf(0.0f, p.tau - alpha * sx_);   // (the two tests may part at a tie)
+    else p.tau -= alpha * sx_;
     ++p.ncross;
     flush_visit<R, F>(A, p);
     const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
     const int stride = axis == 0 ? 1 : (axis == 1 ? A.nx : A.nx * A.ny);
     const int cur = axis == 0 ? p.cx : (axis == 1 ? p.cy : p.cz);
-    // side from the sign of 1/n, which selected the face (see set_dir)
-    const R nd = axis == 0 ? p.ix : (axis == 1 ? p.iy : p.iz);
+    // side from the sign of 1/n, which selected the face
     const int step = nd > (R)0 ? 1 : -1;
     int nc = cur + step;
     int dc = step * stride;
@@ -1085,7 +1126,13 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
         if (bulk && (idle != 0u || ++quiet == kBulkCheck)) {
             quiet = 0;
             const int nidle = __popc(idle);
-            bool leave = *reinterpret_cast<volatile int*>(ctl) != 0;   // one broadcast read
+            // lane 0 reads the flag and broadcasts it: every lane of the warp
+            // must take the same decision (the leave path has a CTA barrier),
+            // and lanes that read it themselves could see it before and after
+            // another warp's write
+            int stop = 0;
+            if (lane == 0) stop = *reinterpret_cast<volatile int*>(ctl);
+            bool leave = __shfl_sync(kFull, stop, 0) != 0;
             if (!leave && (nidle == 32 || (nidle > 0 && nidle >= A.refill_min))) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(A.next, (unsigned long long)nidle);

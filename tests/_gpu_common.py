@@ -170,6 +170,21 @@ def _minus(a, b):
     return a.astype(np.float64) - b.astype(np.float64)
 
 
+def oracle_cell_sums(problem, ids, seed=None):
+    """Per packet: the sum over its scatterings of the flat index of the cell
+    it scattered in (mod 2^32), from the oracle's scattering map of that
+    packet run alone (the record field scat_cells of the FP64 GPU walk)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    idx = np.arange(problem.ncell, dtype=np.uint64)
+
+    def one(i):
+        r = oracle.run(problem, n=1, first=int(i), seed=seed, nthreads=1)
+        return int((r["scat"].astype(np.uint64) * idx).sum() % (1 << 32))
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        return np.array(list(ex.map(one, ids)), dtype=np.uint64)
+
+
 def check_lockstep(krl, problem, gpu, n, first=0, seed=None, min_ok=0.999, label=""):
     """FP64 GPU walk against the oracle on packets [first, first + n):
     per-packet records (status, scatterings, crossings, emission cell) agree
@@ -177,14 +192,24 @@ def check_lockstep(krl, problem, gpu, n, first=0, seed=None, min_ok=0.999, label
     element by element once the packets that diverged are taken out of both
     sides (each side reruns just those ids, one by one, and subtracts them).
 
+    A walk can also part without changing those counts: at a near tie
+    between the remaining optical depth and the distance to a face, one side
+    scatters and then crosses, the other crosses and then scatters at the
+    same point, so one scattering lands in the neighbouring cell (and the
+    frequency re-converges within a few dozen scatterings). When the
+    scattering maps differ, the packets are also compared by the sum of
+    their scattering cells (record field scat_cells against the oracle's
+    per-packet maps), and those that differ count as diverged.
+
     gpu: {"records": structured array, and the tallies of grid_tallies()}.
-    Returns (ok mask, reference run)."""
+    Returns (mask of the packets compared, reference run); the number of
+    packets that differed only in their scattering cells is left in
+    check_lockstep.swapped."""
     import oracle
     ref = oracle.run(problem, n=n, first=first, seed=seed, records=True)
     gr, rr = gpu["records"], ref["records"]
     ok = agreement(gr, rr)
-    nbad = int((~ok).sum())
-    assert ok.mean() >= min_ok, f"{label}: {nbad} of {ok.size} packets diverge"
+    assert ok.mean() >= min_ok, f"{label}: {int((~ok).sum())} of {ok.size} packets diverge"
     # final frequencies: FP32-rounded records against the FP64 oracle. Where the
     # sampler interpolates between a spike row and a bulk row (|x| ~ 2.5-4) the
     # map x_in -> u_par is steep, so FP64 rounding differences can grow over
@@ -194,21 +219,38 @@ def check_lockstep(krl, problem, gpu, n, first=0, seed=None, min_ok=0.999, label
     scale = np.maximum(1.0, np.abs(rr["x"][ok]))
     assert np.mean(dx <= 2e-6 * scale) >= 0.99, label
     assert np.all(dx <= 1e-3 * scale), label
-    g = {k: gpu.get(k) for k in GPU_TALLIES}
-    r = {k: (None if ref[v] is None else np.asarray(ref[v]).reshape(-1)) for k, v in ORACLE_NAME.items()}
-    if nbad:
-        bad = first + np.nonzero(~ok)[0]
+    g0 = {k: gpu.get(k) for k in GPU_TALLIES}
+    r0 = {k: (None if ref[v] is None else np.asarray(ref[v]).reshape(-1)) for k, v in ORACLE_NAME.items()}
+
+    def without(mask):
+        bad = first + np.nonzero(~mask)[0]
+        if bad.size == 0:
+            return g0, r0
         gb = gpu_packets_tallies(krl, problem, bad, krl.KRL_PREC_FP64, seed)
         rb = oracle_packets_tallies(problem, bad, seed)
-        g = {k: _minus(g[k], gb[k]) for k in GPU_TALLIES}
-        r = {k: _minus(r[k], rb[k]) for k in GPU_TALLIES}
+        return ({k: _minus(g0[k], gb[k]) for k in GPU_TALLIES}, {k: _minus(r0[k], rb[k]) for k in GPU_TALLIES})
+
+    g, r = without(ok)
+    swapped = 0
+    if r["scatmap"] is not None and not np.array_equal(g["scatmap"].astype(np.int64), r["scatmap"].astype(np.int64)):
+        # the records agree (the bar above) but some scatterings landed in
+        # neighbouring cells: find those packets by their scattering cells
+        # and take them out too (at most 1 % of the packets, at least one)
+        ids = first + np.nonzero(ok)[0]
+        same = gr["scat_cells"][ok].astype(np.uint64) == oracle_cell_sums(problem, ids, seed)
+        swapped = int((~same).sum())
+        assert swapped <= max(1, n // 100), f"{label}: {swapped} packets scattered in other cells"
+        ok = ok.copy()
+        ok[np.nonzero(ok)[0][~same]] = False
+        g, r = without(ok)
     # counters and integer tallies: identical
     assert np.array_equal(np.asarray(g["stats"])[:7].astype(np.int64), np.asarray(r["stats"])[:7].astype(np.int64)), \
         (label, g["stats"], r["stats"])
     assert np.array_equal(g["spec_n"].astype(np.int64), r["spec_n"].astype(np.int64)), label
     assert np.allclose(g["spec_w"], r["spec_w"], rtol=1e-12, atol=1e-9), label
     if r["scatmap"] is not None:
-        assert np.array_equal(g["scatmap"].astype(np.int64), r["scatmap"].astype(np.int64)), label
+        d = np.nonzero(g["scatmap"].astype(np.int64) != r["scatmap"].astype(np.int64))[0]
+        assert d.size == 0, (label, d[:10], g["scatmap"][d[:10]], r["scatmap"][d[:10]])
     for k in ("exc", "J", "absw"):
         if r[k] is not None:
             ref_k = r[k].astype(np.float64)
@@ -219,4 +261,5 @@ def check_lockstep(krl, problem, gpu, n, first=0, seed=None, min_ok=0.999, label
         # terms then carries up to ~N 2^-24 relative rounding (N ~ 1e4 here).
         e, re_ = g["emiss"].astype(np.float64), r["emiss"]
         assert np.allclose(e, re_, rtol=1e-3, atol=1e-6 * np.abs(re_).max()), label
+    check_lockstep.swapped = swapped
     return ok, ref

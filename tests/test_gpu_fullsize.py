@@ -61,22 +61,6 @@ def test_sphere_full_size(v):
         assert 1e4 < mean < 1e6
 
 
-def test_fp32_against_fp64_at_large_n():
-    """The tau0 = 1e4, a = 0.01 slab at 1e6 packets: the production FP32 walk against the
-    FP64 walk (the instantiation held in lockstep with the oracle), where
-    the two-sample noise floor of the 200-bin spectrum is well below 2 %:
-    relative L1 < 2 % and chi^2 p > 0.01."""
-    krl = need_gpu()
-    p = W.slab(n_packets=1_000_000)
-    f32 = gpu_run(krl, p, krl.KRL_PREC_FP32, records=False)
-    f64 = gpu_run(krl, p, krl.KRL_PREC_FP64, records=False)
-    a, b = f32["spec_n"][1:-1], f64["spec_n"][1:-1]
-    assert rel_l1(a, b) < 0.02, rel_l1(a, b)
-    assert chi2_two_sample(a, b)[2] > 0.01
-    assert f32["stats"].escaped == f64["stats"].escaped == 1_000_000
-    assert abs(f32["stats"].scatterings / f64["stats"].scatterings - 1.0) < 0.01
-
-
 def test_velocity_reversal_mirrors_the_spectrum():
     """With no recoil, reversing every velocity mirrors the problem in
     frequency (x -> -x and u -> -u leave the Voigt profile, the atom-velocity
