@@ -33,14 +33,16 @@ PACKETS_PER_STEP = JOB_PACKETS
 E2E_MAX_STEPS = 3
 METRIC = "scatterings/s & packets/s (64³ τ0=1e6 sphere)"
 UNIT = "scatterings/s"
-# Algorithmic lane operations per event, from the per-unit work estimate of
-# the pass: a scattering = 2 Philox4x32-10 blocks (20 rounds of 2 multiply-
-# high and the xors, ~120 integer ops) + ~8 special-function ops (Box-Muller,
-# isotropic direction, ln xi) + ~14 sampler steps (row choice and search) +
-# ~100 FP32 ops (the upper end of 60-100) = 242; a face crossing = one Voigt
-# lookup (lg2 and interpolation) + ~30 FP32 ops = 32. The measured thread
-# instructions per event (from the ncu summary) give the issue-ceiling
-# fraction beside it.
+# Lane operations per event. The roofline counts the arithmetic operations
+# (integer, FP32, conversion and bit-manipulation instruction classes) that
+# the walk executes per scattering and per face crossing, from the ncu
+# instruction mix of the committed profile (two workloads with different
+# crossing fractions, solved for the two event kinds), used only when that
+# profile was taken on the current kernel source. Beside it: the per-unit
+# work estimate of the pass (a scattering = 2 Philox4x32-10 blocks, ~120
+# integer ops, + ~8 special-function ops + ~14 sampler steps + ~100 FP32 ops
+# = 242; a crossing = one Voigt lookup + ~30 FP32 ops = 32), and the issue
+# ceiling from all executed thread instructions per event.
 OPS_PER_SCAT = 242
 OPS_PER_CROSS = 32
 FP32_LANES_PER_SM = 128
@@ -79,6 +81,8 @@ def parse():
     ap.add_argument("--pixels", type=int, default=512, help="profile case: image side in pixels")
     ap.add_argument("--channels", type=int, default=64, help="profile case: velocity channels")
     ap.add_argument("--launches", type=int, default=1, help="profile case: timed launches")
+    ap.add_argument("--table-space", choices=["shared", "constant"], default="shared",
+                    help="profile case transport: where the walk reads the slice and the sampler")
     return ap.parse_args()
 
 
@@ -149,19 +153,30 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profile_figures():
-    """(DRAM bytes per launch, thread instructions per event) recorded by the
-    committed ncu summary, if it was taken on the current kernel source
-    (else None for both)."""
+PROFILE_KEYS = ("dram_bytes_per_launch_scaled", "thread_instructions_per_event", "thread_instructions_per_scattering",
+                "thread_instructions_per_crossing", "arith_ops_per_scattering", "arith_ops_per_crossing")
+
+
+def profile_values():
+    """The numeric figures of the committed ncu summary (PROFILE_KEYS present
+    in it), if it was taken on the current kernel source; else {}."""
     try:
         txt = open(PROFILE_SUMMARY).read()
         src_hash = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRC)).hexdigest()[:16]
         vals = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith(" "))
         if vals.get("kernel_source_sha256_16", "").strip() != src_hash:
-            return None, None
-        return float(vals["dram_bytes_per_launch_scaled"].strip()), float(vals["thread_instructions_per_event"].strip())
+            return {}
+        return {k: float(vals[k].strip()) for k in PROFILE_KEYS if k in vals}
     except Exception:
-        return None, None
+        return {}
+
+
+def profile_figures():
+    """(DRAM bytes per launch, thread instructions per event) recorded by the
+    committed ncu summary, if it was taken on the current kernel source
+    (else None for both)."""
+    v = profile_values()
+    return v.get("dram_bytes_per_launch_scaled"), v.get("thread_instructions_per_event")
 
 
 def traffic_from_profile():
@@ -172,6 +187,63 @@ RT_GRID = 256
 RT_CHANNELS = 64
 RT_PIXELS = 1024
 RT_CAMERAS = 3
+RT_PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "raytrace_envelope128_64ch.txt")
+RT_KERNEL_SRC = [os.path.join(ROOT, "paper_2608_09340_gb300", "csrc", f) for f in ("raytrace.cu", "krl_internal.cuh")]
+# Arithmetic of one channel-segment of the formal solution (Eq. imaging-
+# formal): dtau = alpha dl, e = exp(-dtau), f = (1 - e)/dtau (2), the
+# increment T j dl f (3), I += it, tau += dtau, T = exp(-tau): 10 ops.
+RT_OPS_PER_CHANNEL_SEGMENT = 10
+
+
+def ray_cells(shape, theta, phi, npix_x, npix_y, fov):
+    """Number of cells each orthographic, pixel-centred ray of a camera at
+    (theta, phi) crosses in a box of shape (nz, ny, nx) (the image centred on
+    the box, fov cells wide): 1 + the face crossings between its entry and
+    exit points. Returns the total over all pixels (a count of the
+    segments the trace marches, for throughput figures)."""
+    import numpy as np
+    nz, ny, nx = shape
+    n = np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)])
+    u = np.array([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)])
+    v = np.array([-np.sin(phi), np.cos(phi), 0.0])
+    pix = fov / npix_x
+    ix = (np.arange(npix_x) + 0.5) * pix - 0.5 * pix * npix_x
+    iy = (np.arange(npix_y) + 0.5) * pix - 0.5 * pix * npix_y
+    uc, vc = np.meshgrid(ix, iy)
+    hi = np.array([nx, ny, nz], dtype=np.float64)
+    P = hi / 2.0 + uc[..., None] * u + vc[..., None] * v
+    t0 = np.full(uc.shape, -np.inf)
+    t1 = np.full(uc.shape, np.inf)
+    inside = np.ones(uc.shape, dtype=bool)
+    for d in range(3):
+        if n[d] != 0.0:
+            a, b = (0.0 - P[..., d]) / n[d], (hi[d] - P[..., d]) / n[d]
+            t0 = np.maximum(t0, np.minimum(a, b))
+            t1 = np.minimum(t1, np.maximum(a, b))
+        else:
+            inside &= (P[..., d] >= 0.0) & (P[..., d] < hi[d])
+    hit = inside & (t1 > t0)
+    eps = 1e-9
+    cells = np.ones(uc.shape)
+    for d in range(3):
+        x0 = np.clip(P[..., d] + (t0 + eps) * n[d], 0.0, hi[d] - 1e-9)
+        x1 = np.clip(P[..., d] + (t1 - eps) * n[d], 0.0, hi[d] - 1e-9)
+        cells += np.abs(np.floor(x1) - np.floor(x0))
+    return float(cells[hit].sum())
+
+
+def rt_profile_values():
+    """Thread instructions per channel-segment of the trace from the committed
+    ray-trace profile, if it was taken on the current source; else {}."""
+    try:
+        txt = open(RT_PROFILE_SUMMARY).read()
+        src_hash = hashlib.sha256(b"".join(open(f, "rb").read() for f in RT_KERNEL_SRC)).hexdigest()[:16]
+        vals = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith(" "))
+        if vals.get("kernel_source_sha256_16", "").split()[0].strip() != src_hash:
+            return {}
+        return {k: float(vals[k].strip()) for k in ("thread_instructions_per_channel_segment",) if k in vals}
+    except Exception:
+        return {}
 
 
 def bench_raytrace(args, dev):
@@ -213,8 +285,22 @@ def bench_raytrace(args, dev):
         g.close()
     rays = RT_CAMERAS * RT_PIXELS * RT_PIXELS
     cube = RT_CAMERAS * RT_GRID ** 3 * RT_CHANNELS * 4
+    segs = sum(ray_cells(p.shape, th, ph, RT_PIXELS, RT_PIXELS, float(RT_GRID)) for th, ph in p.cameras)
+    chseg_per_s = segs * RT_CHANNELS / ms * 1e3
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = measured_peaks()
+    peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    rtp = rt_profile_values()
+    rt_roof = {"bound": "alu", "ops_per_channel_segment": RT_OPS_PER_CHANNEL_SEGMENT,
+               "achieved": RT_OPS_PER_CHANNEL_SEGMENT * chseg_per_s / 1e12, "peak": peak_ops / 1e12,
+               "unit": "Tops/s", "frac": RT_OPS_PER_CHANNEL_SEGMENT * chseg_per_s / peak_ops,
+               "issue_ceiling_frac": (rtp["thread_instructions_per_channel_segment"] * chseg_per_s / peak_ops
+                                      if rtp else None),
+               "thread_instructions_per_channel_segment": rtp.get("thread_instructions_per_channel_segment"),
+               "peak_source": f"{peak_kind} max SM clock"}
     return {"workload": f"envelope {RT_GRID}^3, {RT_CHANNELS} ch, {RT_PIXELS}^2 px, {RT_CAMERAS} inclinations",
             "rays_per_s": rays / ms * 1e3, "channel_rays_per_s": rays * RT_CHANNELS / ms * 1e3,
+            "segments_per_pass": segs, "channel_segments_per_s": chseg_per_s, "roofline": rt_roof,
             "ms_per_pass": ms, "passes": reps,
             "gpu_launches_per_pass": 2 * RT_CAMERAS,      # per camera: profile cube, then the trace
             "emissivity_bytes": cube,
@@ -351,6 +437,27 @@ def bench_next_rows(args, dev):
     modes["mode1_over_mode2"] = modes["ph_mode_1"]["scat_per_s"] / modes["ph_mode_2"]["scat_per_s"]
     out["profile_modes"] = {"workload": "slab 128 cells, a = 0.149, tau_m = 32000, 1e6 packets", **modes}
 
+    # Table placement (Sec. 2.3.1 recommends the constant bank): profile mode 2
+    # with the slice and the sampler read from shared memory (the production
+    # walk) and from the constant bank, on the same slab and on the 64^3,
+    # tau0 = 1e6 sphere (2e4 packets of the benchmark's job)
+    place = {}
+    for wl, q, npk in (("slab", base, 1_000_000), ("sphere64_tau1e6", W.sphere(), 20_000)):
+        g = krl.Grid(q, device=dev)
+        try:
+            row = {}
+            for nm, ts in (("shared", krl.KRL_TABLES_SHARED), ("constant", krl.KRL_TABLES_CONSTANT)):
+                g.run(n=min(npk, 100_000) // 10, first=1 << 40, want_stats=False, table_space=ts)
+                g.reset()
+                dt, st = timed(lambda: g.run(n=npk, first=0, table_space=ts)[0])
+                row[nm] = {"scat_per_s": st.scatterings / dt, "s": dt}
+            row["constant_over_shared"] = row["constant"]["scat_per_s"] / row["shared"]["scat_per_s"]
+            place[wl] = row
+        finally:
+            g.close()
+    out["table_placement"] = {"workloads": "slab as above (1e6 packets); 64^3 tau0 = 1e6 sphere, 2e4 packets",
+                              **place}
+
     # The paper's own timing setup (Sec. 3.5.2, Table 1: uniform 32^3 box,
     # line-centre tau0 = 1e3 from centre to face, T = 100 K, volume source with
     # the thermal profile), for N = 1e3 .. 1e7: the transport launch alone, and
@@ -430,20 +537,22 @@ def profile_case(args):
     k = [0]
     if args.profile_case == "transport":
         p = W.sphere(vmax_kms=args.vmax, tau0=args.tau0)
+        ts = krl.KRL_TABLES_CONSTANT if args.table_space == "constant" else krl.KRL_TABLES_SHARED
         g = krl.Grid(p)
         try:
-            g.run(n=args.packets, first=0, want_stats=False)
+            g.run(n=args.packets, first=0, want_stats=False, table_space=ts)
             g.reset()
 
             def one():
                 k[0] += 1
-                g.run(n=args.packets, first=k[0] * args.packets, want_stats=False)
+                g.run(n=args.packets, first=k[0] * args.packets, want_stats=False, table_space=ts)
             ms = _timed_launches(one, args.launches)
             st = g.tally("stats").cpu().numpy()
         finally:
             g.close()
         scat, cross = int(st[4]), int(st[5])
         out = {"case": "transport", "tau0": args.tau0, "vmax_kms": args.vmax, "packets": args.packets,
+               "table_space": args.table_space,
                "ms_per_launch": ms, "scatterings_per_launch": scat / args.launches,
                "crossings_per_launch": cross / args.launches, "scat_per_s": scat / args.launches / ms * 1e3}
     elif args.profile_case == "emissivity":
@@ -633,22 +742,33 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
-    ops = OPS_PER_SCAT * scat + OPS_PER_CROSS * cross
-    achieved = ops / kern_s
-    traffic, inst_per_event = profile_figures()
+    pv = profile_values()
+    traffic, inst_per_event = pv.get("dram_bytes_per_launch_scaled"), pv.get("thread_instructions_per_event")
+    # per GPU: this rank's events over its own timed region
+    est_frac = (OPS_PER_SCAT * scat + OPS_PER_CROSS * cross) / kern_s / peak_ops
+    if "arith_ops_per_scattering" in pv:
+        ops_s, ops_c, ops_src = pv["arith_ops_per_scattering"], pv["arith_ops_per_crossing"], "ncu instruction mix"
+    else:
+        ops_s, ops_c, ops_src = OPS_PER_SCAT, OPS_PER_CROSS, "per-unit estimate (profile not on this source)"
+    achieved = (ops_s * scat + ops_c * cross) / kern_s
     # issue ceiling: every SM sub-partition issuing one warp instruction per
-    # cycle at full SIMT width, over the measured thread instructions per event
+    # cycle at full SIMT width, over the measured thread instructions per
+    # scattering and per crossing
     issue_frac = None
-    if inst_per_event:
-        ceiling = props.multi_processor_count * 4 * 32 * sm_max * 1e6 / inst_per_event
-        issue_frac = (scat_all + cross_all) / t_max / ceiling
+    if "thread_instructions_per_scattering" in pv:
+        issue_frac = (pv["thread_instructions_per_scattering"] * scat +
+                      pv["thread_instructions_per_crossing"] * cross) / kern_s / peak_ops
+    elif inst_per_event:
+        issue_frac = inst_per_event * (scat + cross) / kern_s / peak_ops
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": achieved / peak_ops, "traffic": traffic, "issue_ceiling_frac": issue_frac,
+            "frac_at_estimated_ops": est_frac, "estimated_ops_per_scattering": OPS_PER_SCAT,
+            "estimated_ops_per_crossing": OPS_PER_CROSS,
             "thread_instructions_per_event": inst_per_event,
             "launch_ms_mean": sum(launch_ms) / len(launch_ms),
             "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                            f"{sm_max:.0f} MHz ({peak_kind} max SM clock)",
-            "ops_per_scattering": OPS_PER_SCAT, "ops_per_crossing": OPS_PER_CROSS}
+            "ops_per_scattering": ops_s, "ops_per_crossing": ops_c, "ops_source": ops_src}
 
     # One more job alone on one stream (no overlap of its tail with another
     # job): the rate a single job gets, beside the streamed rate above.
@@ -667,7 +787,7 @@ def main():
         sec = s0.elapsed_time(s1) / 1e3
         js = int(st_after[4]) - scat
         serial = {"scatterings_per_s": js / sec, "s": sec, "packets": n, "scatterings": js,
-                  "alu_frac": (OPS_PER_SCAT * js + OPS_PER_CROSS * (int(st_after[5]) - cross)) / sec / peak_ops}
+                  "alu_frac": (ops_s * js + ops_c * (int(st_after[5]) - cross)) / sec / peak_ops}
 
     # End to end through the public API with host buffers, jobs streamed the
     # way a user runs several: each job's grid is created from pinned host

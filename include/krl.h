@@ -214,7 +214,18 @@ typedef struct {
                                    cannot be allocated, are deposited by the walk:
                                    the result is the same up to the order of the
                                    FP32 atomic additions                            */
+    int table_space;            /* where the FP32 walk of profile mode 2 reads the
+                                   Voigt slice and the sampler's nodes and ln CDF:
+                                   KRL_TABLES_SHARED (0, default): staged into
+                                   shared memory per CTA; KRL_TABLES_CONSTANT (1):
+                                   the constant bank, the placement Sec. 2.3.1
+                                   recommends (copied in before the launch; runs
+                                   with it must not overlap on the device). For
+                                   measurement; KRL_ERR_ARG for other modes and
+                                   for the FP64 walk                               */
 } krl_tune;
+
+enum { KRL_TABLES_SHARED = 0, KRL_TABLES_CONSTANT = 1 };
 
 /* One record per packet of a run (optional output). */
 typedef struct {

@@ -80,7 +80,7 @@ def trace_maps(oracle_mod, problem, emiss, camera: int, npix_x: int, npix_y: int
     vel = d["vel"]
     tau0 = d["tau0"]
     tau_abs = d["tau_abs"]                                   # continuum opacity, or None
-    em = np.asarray(emiss, dtype=np.float64).reshape(-1, nch)
+    em = np.asarray(emiss).reshape(-1, nch)                 # rows taken to FP64 one segment at a time
     jl = None if jline is None else np.asarray(jline, dtype=np.float64).reshape(-1)
     pix_h = fov / npix_x
     out = np.zeros((nch, npix_y, npix_x))
@@ -99,7 +99,7 @@ def trace_maps(oracle_mod, problem, emiss, camera: int, npix_x: int, npix_y: int
             if tau_abs is not None:                         # line plus continuum extinction
                 alpha = alpha + tau_abs[c]
             dtau = alpha * dl
-            j = em[c].copy()
+            j = em[c].astype(np.float64)
             if jl is not None:
                 j = j + jl[c] * H / SQRT_PI
             e = np.exp(-dtau)

@@ -99,9 +99,13 @@ def levels_desc(E_K, g, A, k_coll, mass_amu, n_mol_tensor) -> krl_levels_desc:
     return d
 
 
+KRL_TABLES_SHARED, KRL_TABLES_CONSTANT = 0, 1
+
+
 class krl_tune(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("ctas_per_sm", C.c_int),
-                ("refill_min", C.c_int), ("max_iters", C.c_uint64), ("emiss_records", C.c_int64)]
+                ("refill_min", C.c_int), ("max_iters", C.c_uint64), ("emiss_records", C.c_int64),
+                ("table_space", C.c_int)]
 
 
 class krl_run_stats(C.Structure):
@@ -323,13 +327,14 @@ class Grid:
 
     def run(self, n: int | None = None, first: int = 0, seed: int | None = None, precision: int = KRL_PREC_FP32,
             records: bool = False, block: int = 0, ctas_per_sm: int = 0, refill_min: int = 0,
-            max_iters: int = 0, want_stats: bool = True, stream=None, emiss_records: int = 0):
+            max_iters: int = 0, want_stats: bool = True, stream=None, emiss_records: int = 0,
+            table_space: int = KRL_TABLES_SHARED):
         """Run packets [first, first+n); returns (stats, status code, records
-        tensor or None). emiss_records: krl_tune.emiss_records."""
+        tensor or None). emiss_records, table_space: krl_tune's fields."""
         import torch
         n = self.problem.n_packets if n is None else int(n)
         seed = self.problem.seed if seed is None else int(seed)
-        tune = krl_tune(precision, block, ctas_per_sm, refill_min, max_iters, emiss_records)
+        tune = krl_tune(precision, block, ctas_per_sm, refill_min, max_iters, emiss_records, table_space)
         rec = None
         if records:
             rec = torch.empty(n * RECORD_DTYPE.itemsize, dtype=torch.uint8, device=self.device)

@@ -312,8 +312,11 @@ bool blend_crossing(double a, double* u0)
 
 krl_status resolve_tune(const krl_tune* tune, krl_tune& T)
 {
-    T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 0xFFFFFFFFull, 0};
+    T = krl_tune{KRL_PREC_FP32, 0, 0, 1, 0xFFFFFFFFull, 0, KRL_TABLES_SHARED};
     if (tune) {
+        if (tune->table_space != KRL_TABLES_SHARED && tune->table_space != KRL_TABLES_CONSTANT)
+            return fail(KRL_ERR_ARG, "unknown table_space %d", tune->table_space);
+        T.table_space = tune->table_space;
         if (tune->emiss_records < -1 || tune->emiss_records > (1ll << 36))
             return fail(KRL_ERR_ARG, "emiss_records must be in [-1, 2^36]");
         T.emiss_records = tune->emiss_records;
@@ -347,7 +350,7 @@ extern "C" {
 
 const char* krl_last_error(void) { return g_err; }
 
-int krl_version(void) { return 400; }       // 0.4.0: krl_batch_run takes per-model record buffers
+int krl_version(void) { return 500; }       // 0.5.0: records carry scat_cells; krl_tune.table_space
 
 krl_status krl_grid_create(krl_grid** out, const krl_grid_desc* d, krl_stream st)
 {
@@ -610,13 +613,21 @@ krl_status krl_run_packets(krl_grid* g, uint64_t n, uint64_t first_id, uint64_t 
     const int maxb = transport_max_block(T.precision, f);
     if (!tune || !tune->block) T.block = maxb;
     else if (T.block > maxb) return fail(KRL_ERR_ARG, "block %d exceeds %d for this walk", T.block, maxb);
-    int occ = transport_occupancy(T.precision, f, T.block, g->line.ph_mode);
+    // constant-bank tables: profile mode 2, FP32 walk (internal mode 4)
+    int mode = g->line.ph_mode;
+    if (T.table_space == KRL_TABLES_CONSTANT) {
+        if (mode != 2 || T.precision != KRL_PREC_FP32)
+            return fail(KRL_ERR_ARG, "table_space = constant needs ph_mode 2 and the FP32 walk");
+        mode = 4;
+    }
+    int occ = transport_occupancy(T.precision, f, T.block, mode);
     if (occ < 1) return fail(KRL_ERR_CUDA, "transport kernel cannot be resident at block %d", T.block);
     int per_sm = T.ctas_per_sm > 0 ? (T.ctas_per_sm < occ ? T.ctas_per_sm : occ) : occ;
     int grid = g->num_sms * per_sm;
 
     TransportArgs A{};
     fill_args(g, A, n, first_id, seed, T, records);
+    A.ph_mode = mode;
     const int slot = (int)(g->run_seq.fetch_add(1u, std::memory_order_relaxed) % kSlots);
     unsigned long long* slot_stats = g->run_stats + (size_t)slot * ST_N;
     unsigned long long* slot_next = g->next + slot;
@@ -836,6 +847,7 @@ krl_status krl_batch_run(krl_batch* b, const uint64_t* packets, const uint64_t* 
     krl_tune T;
     krl_status ts = resolve_tune(tune, T);
     if (ts != KRL_OK) return ts;
+    if (T.table_space != KRL_TABLES_SHARED) return fail(KRL_ERR_ARG, "the batched launch stages its tables in shared memory");
     const unsigned f = b->features;
     const int maxb = transport_batch_max_block();
     if (!T.block) T.block = maxb;

@@ -8,7 +8,7 @@ namespace krl {
 cudaError_t launch_transport(const TransportArgs& A, int precision, unsigned features, int grid, int block,
                              cudaStream_t s)
 {
-    if (A.ph_mode == 1 || A.ph_mode == 3)
+    if (A.ph_mode == 1 || A.ph_mode == 3 || A.ph_mode == 4)
         return launch_transport_ph(A, A.ph_mode, precision, features, grid, block, s);
     return precision == KRL_PREC_FP64 ? dispatch<double, 2>(A, features, grid, block, s)
                                       : dispatch<float, 2>(A, features, grid, block, s);
@@ -47,7 +47,7 @@ int transport_max_block(int precision, unsigned features)
 
 int transport_occupancy(int precision, unsigned features, int block, int ph_mode)
 {
-    if (ph_mode == 1 || ph_mode == 3) return transport_occupancy_ph(ph_mode, precision, features, block);
+    if (ph_mode == 1 || ph_mode == 3 || ph_mode == 4) return transport_occupancy_ph(ph_mode, precision, features, block);
     return precision == KRL_PREC_FP64 ? occ_dispatch<double, 2>(features, block)
                                       : occ_dispatch<float, 2>(features, block);
 }

@@ -45,6 +45,17 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Table placement PH = 4 (a measurement variant of profile mode 2, chosen
+// by krl_tune.table_space): the Voigt slice and the sampler's nodes and ln
+// CDF read from __constant__ memory (60 KB, copied in before each launch)
+// instead of shared memory; the search guides stay in shared memory. The
+// arrays exist only in the translation unit that instantiates that mode.
+#ifdef KRL_TABLES_IN_CONSTANT
+__constant__ float c_voigt[kVoigtN];
+__constant__ float c_usx[kUsNx];
+__constant__ float c_uslncdf[kUsNx * kUsNu];
+#endif
+
 // ---------------------------------------------------------------- Philox4x32-10
 
 struct Words {
@@ -209,6 +220,7 @@ __device__ __forceinline__ R blend(const TransportArgs& A, R x, R a)
 template <typename R, int PH>
 __device__ __forceinline__ R profile(const TransportArgs& A, R x, const float* sv, R a, R H0)
 {
+    // (PH 4 is mode 2 with its tables in constant memory: the slice below)
     if constexpr (PH == 1) return voigt2d<R>(A, x, a);
     else if constexpr (PH == 3) return blend<R>(A, x, a);
     else return voigt<R>(x, sv, a, H0);
@@ -1082,9 +1094,11 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
     if constexpr (PH == 2) {
         for (int i = threadIdx.x; i < kVoigtN; i += blockDim.x) sm[kSmemVoigt + i] = A.voigt_lnH[i];
     }
-    if constexpr (PH != 1) {
+    if constexpr (PH == 2 || PH == 3) {
         for (int i = threadIdx.x; i < kUsNx; i += blockDim.x) sm[kSmemUsX + i] = A.us_x[i];
         for (int i = threadIdx.x; i < kUsNx * kUsNu; i += blockDim.x) sm[kSmemUsC + i] = A.us_lncdf[i];
+    }
+    if constexpr (PH != 1) {
         for (int i = threadIdx.x; i < kUsNx * kGuideN; i += blockDim.x) sgw[i] = A.us_guide[i];
     }
     if (threadIdx.x == 0) ctl[0] = 0;
@@ -1092,6 +1106,13 @@ __device__ __forceinline__ void run_model(const TransportArgs& A, const RoundKey
     const float* sv = sm + kSmemVoigt;
     const float* sx = PH == 1 ? A.us_x : sm + kSmemUsX;
     const float* sc = PH == 1 ? A.us_lncdf : sm + kSmemUsC;
+#ifdef KRL_TABLES_IN_CONSTANT
+    if constexpr (PH == 4) {
+        sv = c_voigt;
+        sx = c_usx;
+        sc = c_uslncdf;
+    }
+#endif
     const unsigned char* sg = PH == 1 ? A.us_guide : sgw;
     // the sampler's row guide, from the staged nodes (all profile modes)
     unsigned char* rgw = reinterpret_cast<unsigned char*>(sm) + kSmemRowGuide;

@@ -47,10 +47,39 @@ def test_profile_figures_follow_the_kernel_source(tmp_path, monkeypatch):
     h = hashlib.sha256(b"kernel akernel b").hexdigest()[:16]
     summary = tmp_path / "profile.txt"
     summary.write_text(f"kernel: k\nkernel_source_sha256_16: {h}\ndram_bytes_per_launch_scaled: 6096000\n"
-                       "thread_instructions_per_event: 411\n  indented: not a key\n")
+                       "thread_instructions_per_event: 411\narith_ops_per_scattering: 286.4\n"
+                       "arith_ops_per_crossing: 181.0\n  indented: not a key\n")
     monkeypatch.setattr(bench, "KERNEL_SRC", srcs)
     monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(summary))
     assert bench.profile_figures() == (6096000.0, 411.0)
     assert bench.traffic_from_profile() == 6096000.0
+    v = bench.profile_values()
+    assert v["arith_ops_per_scattering"] == 286.4 and v["arith_ops_per_crossing"] == 181.0
+    assert "thread_instructions_per_scattering" not in v
     (tmp_path / "k1.cuh").write_bytes(b"kernel b changed")
     assert bench.profile_figures() == (None, None)
+    assert bench.profile_values() == {}
+
+
+def test_ray_cell_count_equals_the_oracle_walk():
+    """The closed-form count of the cells each orthographic ray crosses (the
+    ray trace's channel-segment throughput) equals the number of
+    positive-length segments of the oracle's cell walk, ray by ray summed,
+    for oblique and axis-aligned cameras."""
+    import math
+    import numpy as np
+    import oracle
+    from oracle import raytrace as RT
+    shape = (5, 6, 7)
+    npx, npy, fov = 9, 8, 8.0
+    for th, ph in [(0.3, 0.7), (1.1, 2.0), (0.0, 0.0), (math.pi / 2, 0.0), (2.5, -1.0)]:
+        n, u, v = RT.camera_basis(th, ph)
+        C = np.array([shape[2], shape[1], shape[0]]) / 2.0
+        pix = fov / npx
+        tot = 0
+        for iy in range(npy):
+            for ix in range(npx):
+                P = C + ((ix + 0.5) * pix - 0.5 * fov) * u + ((iy + 0.5) * pix - 0.5 * pix * npy) * v
+                _, lens = RT.ray_segments(oracle, shape, (False,) * 3, P, n)
+                tot += int((lens > 0).sum())
+        assert bench.ray_cells(shape, th, ph, npx, npy, fov) == tot

@@ -126,3 +126,47 @@ def test_modes_rejected_where_unsupported():
             krl.Batch([g])
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("name", ["sphere_static", "sphere_moving", "envelope"])
+def test_constant_table_placement_is_the_same_walk(name):
+    """krl_tune.table_space = constant (the slice and the sampler read from
+    the constant bank, the placement Sec. 2.3.1 recommends) runs the same
+    FP32 walk as the shared-memory staging: records and integer tallies
+    identical, FP tallies equal up to the order of their atomic additions."""
+    krl = need_gpu()
+    p = {"sphere_static": W.sphere(tau0=1e4, n=16, n_packets=4000),
+         "sphere_moving": W.sphere(vmax_kms=150.0, tau0=3e4, n=24, n_packets=4000),
+         "envelope": W.envelope(n=16, n_ch=16, n_packets=3000)}[name]
+    a = gpu_run(krl, p, krl.KRL_PREC_FP32)
+    b = gpu_run(krl, p, krl.KRL_PREC_FP32, table_space=krl.KRL_TABLES_CONSTANT)
+    for f in a["records"].dtype.names:
+        assert np.array_equal(a["records"][f], b["records"][f]), f
+    assert np.array_equal(a["spec_n"], b["spec_n"])
+    for k in ("scatmap", "stats_tally"):
+        if a[k] is not None:
+            assert np.array_equal(a[k], b[k]), k
+    for k in ("exc", "J", "emiss"):
+        if a[k] is not None:
+            assert np.allclose(a[k], b[k], rtol=1e-3, atol=1e-6 * np.abs(a[k]).max()), k
+
+
+def test_constant_table_placement_is_rejected_where_unsupported():
+    krl = need_gpu()
+    g = krl.Grid(W.slab(tau0=1e3, n_packets=8))
+    try:
+        with pytest.raises(krl.KrlError) as e:
+            g.run(precision=krl.KRL_PREC_FP64, table_space=krl.KRL_TABLES_CONSTANT)
+        assert e.value.status == krl.KRL_ERR_ARG
+        with pytest.raises(krl.KrlError) as e:
+            g.run(table_space=7)
+        assert e.value.status == krl.KRL_ERR_ARG
+    finally:
+        g.close()
+    g = krl.Grid(_mode(W.slab(tau0=1e3, n_packets=8), 1))
+    try:
+        with pytest.raises(krl.KrlError) as e:
+            g.run(table_space=krl.KRL_TABLES_CONSTANT)
+        assert e.value.status == krl.KRL_ERR_ARG
+    finally:
+        g.close()
