@@ -430,9 +430,11 @@ typedef struct {
  * [n_ch][npix_y][npix_x], written (raw units: emissivity x cell widths).
  * All faces are open for the rays. Enqueued on `s`; does not synchronise.
  * alpha_k depends on the cell and the channel only, so it is tabulated once
- * per call in a stream-ordered scratch of ncell x n_ch floats (cudaMallocAsync
- * on `s`, freed on `s` after the trace); with no_scratch, or when that memory
- * is not available, the trace evaluates H per segment, with the same result.
+ * per call in a stream-ordered scratch of ncell x n_ch floats, beside each
+ * ray's starting cell and position (32 bytes per pixel, set up in FP64 once
+ * per ray) (cudaMallocAsync on `s`, freed on `s` after the trace); with
+ * no_scratch, or when that memory is not available, the trace evaluates H per
+ * segment and each ray's lanes set it up themselves, with the same result.
  */
 KRL_API krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float* maps, krl_stream s);
 

@@ -168,9 +168,13 @@ def derive(problem):
 
 
 def run(problem, n: int | None = None, first: int = 0, seed: int | None = None,
-        nthreads: int | None = None, records: bool = False, max_iters: int = 1 << 40,
+        nthreads: int | None = None, records: bool = False, max_iters: int = (1 << 32) - 1,
         tables: dict | None = None):
     """Run packets [first, first+n) of `problem` through the FP64 walk.
+
+    max_iters: per-packet event budget; the default is the library's
+    (2^32 - 1, the largest the CUDA walk accepts), so both stop a packet at
+    the same event.
 
     Returns a dict: spec_w, spec_c (under, bins, over), scat, exc, J, emiss
     (raw sums with unit packet weight, lengths in cell widths), absw (weight

@@ -736,6 +736,10 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
     A.v[0] = -sin(ph);
     A.v[1] = cos(ph);
     A.v[2] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        A.dirf[k] = (float)(-A.n[k]);
+        A.invf[k] = 1.0f / A.dirf[k];
+    }
     A.centre[0] = 0.5 * g->nx;
     A.centre[1] = 0.5 * g->ny;
     A.centre[2] = 0.5 * g->nz;
@@ -747,12 +751,15 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
     // streams never share it). Without the memory the trace evaluates the
     // profile per segment instead, with the same result.
     cudaStream_t s = (cudaStream_t)st;
-    const size_t hbytes = (size_t)g->ncell * (size_t)L.n_ch * sizeof(float);
+    const size_t hbytes = ((size_t)g->ncell * (size_t)L.n_ch * sizeof(float) + 255) / 256 * 256;
+    const size_t rbytes = (size_t)d->npix_x * (size_t)d->npix_y * 2 * sizeof(float4);
     A.hcube = nullptr;
-    if (!d->no_scratch && cudaMallocAsync((void**)&A.hcube, hbytes, s) != cudaSuccess) {
+    A.rayinit = nullptr;
+    if (!d->no_scratch && cudaMallocAsync((void**)&A.hcube, hbytes + rbytes, s) != cudaSuccess) {
         (void)cudaGetLastError();
         A.hcube = nullptr;
     }
+    if (A.hcube) A.rayinit = reinterpret_cast<float4*>(reinterpret_cast<char*>(A.hcube) + hbytes);
     cudaError_t e = launch_raytrace(A, g->num_sms, s);
     if (A.hcube) {
         cudaError_t ef = cudaFreeAsync(A.hcube, s);

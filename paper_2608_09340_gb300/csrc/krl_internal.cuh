@@ -199,9 +199,12 @@ struct RayArgs {
     const float* jline;       // [ncell] frequency-integrated line emission, or nullptr
     float* hcube;             // [ncell][n_ch] scratch for the per-camera profile, or nullptr
                               // (then the trace evaluates the profile per segment)
+    float4* rayinit;          // with hcube: [npix][2] scratch for each ray's start
+                              // ({cell x, y, z, hit} as ints, {in-cell x, y, z, -})
     int n_ch;
     double ch_x0, ch_dx;      // v_min / b, dv / b
     double n[3], u[3], v[3];  // camera direction and image axes
+    float dirf[3], invf[3];   // the march direction -n in float and its reciprocal
     double centre[3];         // image centre (box centre), cell units
     double pix;               // pixel size, cell units
     int npix_x, npix_y;

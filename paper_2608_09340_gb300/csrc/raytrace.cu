@@ -162,6 +162,54 @@ __global__ void __launch_bounds__(256) k_rt_profile(const RayArgs A, float* hc)
     }
 }
 
+// Each ray's start on the camera-side face of the box, one thread per ray
+// (FP64: the entry point fixes the segment lengths of the whole ray): the
+// first cell and the position inside it, or no hit. The trace's lanes read
+// their ray's record instead of repeating this setup per lane.
+__global__ void __launch_bounds__(256) k_ray_setup(const RayArgs A)
+{
+    const long long ray = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long npix = (long long)A.npix_x * A.npix_y;
+    if (ray >= npix) return;
+    const int ix = (int)(ray % A.npix_x);
+    const int iy = (int)(ray / A.npix_x);
+    const double uc = (ix + 0.5) * A.pix - 0.5 * A.pix * A.npix_x;
+    const double vc = (iy + 0.5) * A.pix - 0.5 * A.pix * A.npix_y;
+    double P[3];
+    for (int d = 0; d < 3; ++d) P[d] = A.centre[d] + uc * A.u[d] + vc * A.v[d];
+    const double hi[3] = {(double)A.nx, (double)A.ny, (double)A.nz};
+    double t0 = -1e300, t1 = 1e300;
+    bool hit = true;
+    for (int d = 0; d < 3; ++d) {
+        if (A.n[d] != 0.0) {
+            double ta = (0.0 - P[d]) / A.n[d], tb = (hi[d] - P[d]) / A.n[d];
+            t0 = fmax(t0, fmin(ta, tb));
+            t1 = fmin(t1, fmax(ta, tb));
+        } else if (!(P[d] >= 0.0 && P[d] < hi[d])) {
+            hit = false;
+        }
+    }
+    hit = hit && t1 > t0;
+    int ci[3] = {0, 0, 0};
+    float p[3] = {0.0f, 0.0f, 0.0f};
+    if (hit) {
+        for (int d = 0; d < 3; ++d) {
+            double X = fmin(hi[d], fmax(0.0, P[d] + t1 * A.n[d]));
+            double f = floor(X);
+            int c = (int)f;
+            double r = X - f;
+            const float dir = (float)(-A.n[d]);
+            if (r == 0.0 && dir < 0.0f) { c -= 1; r = 1.0; }
+            if (c >= (int)hi[d]) { c = (int)hi[d] - 1; r = 1.0; }
+            ci[d] = c;
+            p[d] = (float)r;
+        }
+    }
+    A.rayinit[2 * ray] = make_float4(__int_as_float(ci[0]), __int_as_float(ci[1]), __int_as_float(ci[2]),
+                                     __int_as_float(hit ? 1 : 0));
+    A.rayinit[2 * ray + 1] = make_float4(p[0], p[1], p[2], 0.0f);
+}
+
 // (1 - e^{-d})/d and e^{-d} without a branch: the exponential form above
 // d = 0.05, the series below.
 __device__ __forceinline__ float escape_factor_bf(float d)
@@ -180,7 +228,7 @@ __device__ __forceinline__ float escape_factor_bf(float d)
 // cube holds the extinction alpha0 H + alpha_abs (JL false) or H (JL true:
 // the line-emission term needs H; alpha is formed here).
 template <int LPR, bool JL>
-__global__ void __launch_bounds__(256) k_trace_cube(const RayArgs A)
+__global__ void __launch_bounds__(256, 6) k_trace_cube(const RayArgs A)
 {
     constexpr int CPL = 4;
     const int lane = threadIdx.x & 31;
@@ -191,44 +239,18 @@ __global__ void __launch_bounds__(256) k_trace_cube(const RayArgs A)
     const int ix = (int)(ray % A.npix_x);
     const int iy = (int)(ray / A.npix_x);
 
-    // ray setup in FP64: pixel centre on the image plane, box entry/exit
-    const double uc = (ix + 0.5) * A.pix - 0.5 * A.pix * A.npix_x;
-    const double vc = (iy + 0.5) * A.pix - 0.5 * A.pix * A.npix_y;
-    double P[3], n[3];
-    for (int d = 0; d < 3; ++d) {
-        P[d] = A.centre[d] + uc * A.u[d] + vc * A.v[d];
-        n[d] = A.n[d];
-    }
-    const double hi[3] = {(double)A.nx, (double)A.ny, (double)A.nz};
-    double t0 = -1e300, t1 = 1e300;
-    bool hit = true;
-    for (int d = 0; d < 3; ++d) {
-        if (n[d] != 0.0) {
-            double ta = (0.0 - P[d]) / n[d], tb = (hi[d] - P[d]) / n[d];
-            t0 = fmax(t0, fmin(ta, tb));
-            t1 = fmin(t1, fmax(ta, tb));
-        } else if (!(P[d] >= 0.0 && P[d] < hi[d])) {
-            hit = false;
-        }
-    }
+    // the ray's start (k_ray_setup): first cell, position in it, hit
+    const float4 r0 = __ldg(A.rayinit + 2 * ray), r1 = __ldg(A.rayinit + 2 * ray + 1);
     float I[CPL], Ic[CPL], tau[CPL], tc[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) I[q] = Ic[q] = tau[q] = tc[q] = 0.0f;
 
-    if (hit && t1 > t0) {
-        int ci[3];
-        float p[3], dir[3], inv[3];
-        for (int d = 0; d < 3; ++d) {
-            double X = fmin(hi[d], fmax(0.0, P[d] + t1 * n[d]));
-            double f = floor(X);
-            int c = (int)f;
-            double r = X - f;
-            dir[d] = (float)(-n[d]);
-            if (r == 0.0 && dir[d] < 0.0f) { c -= 1; r = 1.0; }
-            if (c >= (int)hi[d]) { c = (int)hi[d] - 1; r = 1.0; }
-            ci[d] = c;
-            p[d] = (float)r;
-            inv[d] = 1.0f / dir[d];
+    if (__float_as_int(r0.w)) {
+        int ci[3] = {__float_as_int(r0.x), __float_as_int(r0.y), __float_as_int(r0.z)};
+        float p[3] = {r1.x, r1.y, r1.z}, dir[3], inv[3];
+        for (int d = 0; d < 3; ++d) {        // (from the parameter block: no FP64 per ray)
+            dir[d] = A.dirf[d];
+            inv[d] = A.invf[d];
         }
         const int max_seg = A.nx + A.ny + A.nz + 3;
         for (int seg = 0; seg < max_seg; ++seg) {
@@ -413,6 +435,7 @@ cudaError_t launch_cpl(const RayArgs& A, int sm_count, cudaStream_t s)
     if (A.hcube) {
         const long long blocks = (npix * LPR + 255) / 256;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        k_ray_setup<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(A);
         if (A.jline) {
             k_rt_profile<CPL, false><<<sm_count * 8, 256, 0, s>>>(A, A.hcube);
             k_trace_cube<LPR, true><<<(unsigned)blocks, 256, 0, s>>>(A);
