@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-raytrace", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-full-range", action="store_true",
+                    help="also time the many-model set over its full tau0 range [1e3, 1e7] (2e5 packets; "
+                         "several minutes), batched against one launch per model")
     ap.add_argument("--no-next", action="store_true", help="skip the levels / profile-mode / dusty-slab legs")
     ap.add_argument("--streams", type=int, default=2,
                     help="streams the steps rotate over (1: no overlap of one step's tail with the next)")
@@ -319,18 +322,22 @@ BATCH_PACKETS = 300_000
 BATCH_TAU = (1e3, 1e5)
 
 
-def bench_batch(args, dev):
+def bench_batch(args, dev, tau_range=None, total_packets=None, with_graph=True, tuned=None):
     """The many-model set at the scaled size (64 uniform spheres, sides in
     {32, 48, 64, 96, 128}, tau0 log-uniform in [1e3, 1e5], a log-uniform in
     [1e-4, 1e-2], v_max uniform in [-300, 300] km/s, 3e5 packets split in
     proportion to tau0): one persistent batched launch (launch parameters
     from the autotuner), the same launch replayed from a CUDA graph, and one
-    launch per model on one stream, each over the same packets."""
+    launch per model on one stream, each over the same packets. tau_range
+    and total_packets override the scaled set's, and tuned skips the
+    autotuner (the full-range leg reuses the scaled set's choice)."""
+    tau_range = tau_range or BATCH_TAU
+    total_packets = total_packets or BATCH_PACKETS
     import torch
     import paper_2608_09340_gb300 as krl
     from paper_2608_09340_gb300 import autotune
     import workloads as W
-    ms = W.model_set(n_models=BATCH_MODELS, total_packets=BATCH_PACKETS, tau_range=BATCH_TAU)
+    ms = W.model_set(n_models=BATCH_MODELS, total_packets=total_packets, tau_range=tau_range)
     grids = [krl.Grid(p, device=dev) for p in ms]
     pk = [p.n_packets for p in ms]
     stream = torch.cuda.current_stream(dev)
@@ -349,21 +356,23 @@ def bench_batch(args, dev):
 
     try:
         b = krl.Batch(grids)
-        best, _ = autotune.tune_batch(b, pk)
+        best = tuned if tuned is not None else autotune.tune_batch(b, pk)[0]
         b.run(pk, seed=7, **best)                                  # warm-up
         for g in grids:
             g.reset()
         t_batch = timed(lambda: b.run(pk, seed=7, **best))
         scat = total_scat()
-        for g in grids:
-            g.reset()
-        s = torch.cuda.Stream(device=dev)
-        graph = torch.cuda.CUDAGraph()
-        torch.cuda.synchronize(dev)
-        with torch.cuda.graph(graph, stream=s):
-            b.run(pk, seed=7, stream=s, **best)
-        t_graph = timed(lambda: graph.replay())
-        assert total_scat() == scat
+        t_graph = None
+        if with_graph:
+            for g in grids:
+                g.reset()
+            s = torch.cuda.Stream(device=dev)
+            graph = torch.cuda.CUDAGraph()
+            torch.cuda.synchronize(dev)
+            with torch.cuda.graph(graph, stream=s):
+                b.run(pk, seed=7, stream=s, **best)
+            t_graph = timed(lambda: graph.replay())
+            assert total_scat() == scat
         for g in grids:
             g.reset()
         t_single = timed(lambda: [g.run(n=n, seed=7, want_stats=False) for g, n in zip(grids, pk)])
@@ -372,9 +381,9 @@ def bench_batch(args, dev):
     finally:
         for g in grids:
             g.close()
-    return {"workload": f"{BATCH_MODELS} spheres, tau0 log-U{list(BATCH_TAU)}, {BATCH_PACKETS} packets",
+    return {"workload": f"{BATCH_MODELS} spheres, tau0 log-U{list(tau_range)}, {total_packets} packets",
             "scatterings": scat, "tuned": best,
-            "batched_scat_per_s": scat / t_batch, "graph_scat_per_s": scat / t_graph,
+            "batched_scat_per_s": scat / t_batch, "graph_scat_per_s": scat / t_graph if t_graph else None,
             "per_model_scat_per_s": scat / t_single, "speedup_vs_per_model": t_single / t_batch,
             "s_batched": t_batch, "s_graph": t_graph, "s_per_model": t_single}
 
@@ -439,10 +448,11 @@ def bench_next_rows(args, dev):
 
     # Table placement (Sec. 2.3.1 recommends the constant bank): profile mode 2
     # with the slice and the sampler read from shared memory (the production
-    # walk) and from the constant bank, on the same slab and on the 64^3,
-    # tau0 = 1e6 sphere (2e4 packets of the benchmark's job)
+    # walk) and from the constant bank, on the same slab and on the 64^3
+    # sphere at tau0 = 1e4 (2^19 packets: enough that the launch is not set
+    # by its longest packets, as a short tau0 = 1e6 run would be)
     place = {}
-    for wl, q, npk in (("slab", base, 1_000_000), ("sphere64_tau1e6", W.sphere(), 20_000)):
+    for wl, q, npk in (("slab", base, 1_000_000), ("sphere64_tau1e4", W.sphere(tau0=1e4), 1 << 19)):
         g = krl.Grid(q, device=dev)
         try:
             row = {}
@@ -455,7 +465,7 @@ def bench_next_rows(args, dev):
             place[wl] = row
         finally:
             g.close()
-    out["table_placement"] = {"workloads": "slab as above (1e6 packets); 64^3 tau0 = 1e6 sphere, 2e4 packets",
+    out["table_placement"] = {"workloads": "slab as above (1e6 packets); 64^3 tau0 = 1e4 sphere, 2^19 packets",
                               **place}
 
     # The paper's own timing setup (Sec. 3.5.2, Table 1: uniform 32^3 box,
@@ -844,6 +854,9 @@ def main():
     bt = None
     if rank == 0 and not args.no_batch:
         bt = bench_batch(args, dev)
+        if args.batch_full_range:
+            bt["full_range"] = bench_batch(args, dev, tau_range=(1e3, 1e7), total_packets=200_000, with_graph=False,
+                                           tuned=bt["tuned"])
     nx = None
     if rank == 0 and not args.no_next:
         nx = bench_next_rows(args, dev)
