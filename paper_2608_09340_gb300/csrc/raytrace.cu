@@ -220,6 +220,49 @@ __device__ __forceinline__ float escape_factor_bf(float d)
     return d > 0.05f ? lg : sm;
 }
 
+// Two channels at a time with the paired FP32 instructions (sm_100 and
+// later; each half rounds as the single-precision operation would). a - b
+// is formed as fma(b, -1, a), exact in the product and rounded once.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+__device__ __forceinline__ void kahan_add2(float2& sum, float2& comp, float2 v)
+{
+    const float2 y = sub2(v, comp);
+    const float2 t = __fadd2_rn(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
+// e^{-x} of two values as 2^(-x log2 e), with the hardware's approximate
+// base-2 exponential
+__device__ __forceinline__ float2 exp_neg2(float2 x)
+{
+    const float2 m = __fmul2_rn(x, make_float2(-1.4426950408889634f, -1.4426950408889634f));
+    float2 r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(m.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(m.y));
+    return r;
+}
+
+// (1 - e^{-d})/d of two values without a branch: from e^{-d} above d = 0.05,
+// else its Taylor series 1 - d/2 + d^2/6 - d^3/24 + d^4/120 (Horner in d)
+__device__ __forceinline__ float2 escape_factor2(float2 d)
+{
+    const float2 e = exp_neg2(d);
+    float2 rd;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd.x) : "f"(d.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd.y) : "f"(d.y));
+    const float2 lg = __fmul2_rn(sub2(make_float2(1.0f, 1.0f), e), rd);
+    float2 sm = __ffma2_rn(make_float2(1.0f / 120.0f, 1.0f / 120.0f), d, make_float2(-1.0f / 24.0f, -1.0f / 24.0f));
+    sm = __ffma2_rn(sm, d, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+    sm = __ffma2_rn(sm, d, make_float2(-0.5f, -0.5f));
+    sm = __ffma2_rn(sm, d, make_float2(1.0f, 1.0f));
+    return make_float2(d.x > 0.05f ? lg.x : sm.x, d.y > 0.05f ? lg.y : sm.y);
+}
+
 // The trace over the per-camera cube (k_rt_profile): LPR lanes per ray, 4
 // channels per lane (lane l of a ray holds channels l + LPR q, q < 4), so a
 // warp follows 32 / LPR neighbouring rays, whose walks through the grid
@@ -228,7 +271,7 @@ __device__ __forceinline__ float escape_factor_bf(float d)
 // cube holds the extinction alpha0 H + alpha_abs (JL false) or H (JL true:
 // the line-emission term needs H; alpha is formed here).
 template <int LPR, bool JL>
-__global__ void __launch_bounds__(256, 6) k_trace_cube(const RayArgs A)
+__global__ void __launch_bounds__(256, 5) k_trace_cube(const RayArgs A)
 {
     constexpr int CPL = 4;
     const int lane = threadIdx.x & 31;
@@ -241,9 +284,11 @@ __global__ void __launch_bounds__(256, 6) k_trace_cube(const RayArgs A)
 
     // the ray's start (k_ray_setup): first cell, position in it, hit
     const float4 r0 = __ldg(A.rayinit + 2 * ray), r1 = __ldg(A.rayinit + 2 * ray + 1);
-    float I[CPL], Ic[CPL], tau[CPL], tc[CPL];
+    // channels (2h, 2h + 1) of this lane in pair h: intensity, optical depth
+    // in front of the segment, and their compensation terms
+    float2 I[CPL / 2], Ic[CPL / 2], tau[CPL / 2], tc[CPL / 2];
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) I[q] = Ic[q] = tau[q] = tc[q] = 0.0f;
+    for (int h = 0; h < CPL / 2; ++h) I[h] = Ic[h] = tau[h] = tc[h] = make_float2(0.0f, 0.0f);
 
     if (__float_as_int(r0.w)) {
         int ci[3] = {__float_as_int(r0.x), __float_as_int(r0.y), __float_as_int(r0.z)};
@@ -270,22 +315,21 @@ __global__ void __launch_bounds__(256, 6) k_trace_cube(const RayArgs A)
                 ta = A.tau_abs ? __ldg(A.tau_abs + c) : 0.0f;
                 jl = __ldg(A.jline + c) * 0.56418958354775628f;
             }
+            const float2 s2 = make_float2(s, s);
 #pragma unroll
-            for (int q = 0; q < CPL; ++q) {
-                const int k = sub + LPR * q;
-                if (k < A.n_ch) {
-                    const float v = __ldg(arow + k);
-                    float j = __ldg(jrow + k);
-                    float alpha = v;
-                    if (JL) {
-                        alpha = fmaf(a0, v, ta);
-                        j = fmaf(jl, v, j);
-                    }
-                    const float dtau = alpha * s;
-                    const float T = __expf(-tau[q]);
-                    kahan_add(I[q], Ic[q], T * j * s * escape_factor_bf(dtau));
-                    kahan_add(tau[q], tc[q], dtau);
+            for (int h = 0; h < CPL / 2; ++h) {
+                // channels past n_ch read zeros: dtau = 0 and no intensity
+                const int ka = sub + LPR * (2 * h), kb = ka + LPR;
+                float2 v = make_float2(ka < A.n_ch ? __ldg(arow + ka) : 0.0f, kb < A.n_ch ? __ldg(arow + kb) : 0.0f);
+                float2 j = make_float2(ka < A.n_ch ? __ldg(jrow + ka) : 0.0f, kb < A.n_ch ? __ldg(jrow + kb) : 0.0f);
+                if (JL) {
+                    j = __ffma2_rn(make_float2(jl, jl), v, j);
+                    v = __ffma2_rn(make_float2(a0, a0), v, make_float2(ta, ta));
                 }
+                const float2 dtau = __fmul2_rn(v, s2);
+                const float2 T = exp_neg2(tau[h]);
+                kahan_add2(I[h], Ic[h], __fmul2_rn(__fmul2_rn(__fmul2_rn(T, j), s2), escape_factor2(dtau)));
+                kahan_add2(tau[h], tc[h], dtau);
             }
             for (int d = 0; d < 3; ++d)
                 if (d != axis) p[d] = fminf(1.0f, fmaxf(0.0f, fmaf(s, dir[d], p[d])));
@@ -295,9 +339,10 @@ __global__ void __launch_bounds__(256, 6) k_trace_cube(const RayArgs A)
         }
     }
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-        const int k = sub + LPR * q;
-        if (k < A.n_ch) A.maps[((size_t)k * A.npix_y + iy) * A.npix_x + ix] = I[q];
+    for (int h = 0; h < CPL / 2; ++h) {
+        const int ka = sub + LPR * (2 * h), kb = ka + LPR;
+        if (ka < A.n_ch) A.maps[((size_t)ka * A.npix_y + iy) * A.npix_x + ix] = I[h].x;
+        if (kb < A.n_ch) A.maps[((size_t)kb * A.npix_y + iy) * A.npix_x + ix] = I[h].y;
     }
 }
 
