@@ -142,6 +142,80 @@ struct Ops<double> {
     }
 };
 
+// ---------------------------------------------------------------- paired FP32 draws
+//
+// The FP32 walk pairs the independent single-precision work of a scattering
+// in the paired instructions of sm_100 and later (FFMA2 / FADD2 / FMUL2;
+// each half rounds as the scalar operation would): the uniforms, the logs,
+// the two angles, the square roots' products and the Box-Muller and
+// direction products, and the two sampler rows' inversions.
+
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// a - b for two values as fma(b, -1, a): exact product, one rounding
+__device__ __forceinline__ float2 sub2f(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+// two uniforms ((r >> 9) + 1/2) 2^-23, as Ops<float>::uni
+__device__ __forceinline__ float2 uni2(uint32_t a, uint32_t b)
+{
+    return __fadd2_rn(make_float2(__uint_as_float((a >> 9) + 0x3f800000u), __uint_as_float((b >> 9) + 0x3f800000u)),
+                      make_float2(-0x1.fffffep-1f, -0x1.fffffep-1f));
+}
+
+// One scattering's draws from its two Philox blocks (slots as in advance):
+// the guide bin and L = ln(xi) of the velocity sampler, the Box-Muller
+// radius and phase (cos, sin), the new isotropic direction, the next free
+// path.
+struct DrawsF {
+    float L, rad, bc, bs, mx, my, mz, tau;
+    int gm;
+};
+
+__device__ __forceinline__ DrawsF draws_f32(const Words& w0, const Words& w1)
+{
+    constexpr float kLn2 = 0.69314718055994531f;
+    DrawsF D;
+    const float2 ua = uni2(w0.w[0], w0.w[1]);          // xi of u_par, Box-Muller radius
+    const float2 ub = uni2(w0.w[2], w0.w[3]);          // Box-Muller phase, free path
+    const float2 uc = uni2(w1.w[0], w1.w[1]);          // mu, azimuth
+    // -ln of the radius and free-path uniforms; ln xi and ln(1 - xi)
+    const float2 nl = __fmul2_rn(make_float2(lg2_approx(ua.y), lg2_approx(ub.y)), make_float2(-kLn2, -kLn2));
+    const float2 lx = __fmul2_rn(make_float2(lg2_approx(ua.x), lg2_approx(1.0f - ua.x)), make_float2(kLn2, kLn2));
+    D.L = fminf(lx.x, -1e-30f);
+    int m = (int)((D.L - lx.y + (float)kGuideW) * (float)(kGuideN / (2.0 * kGuideW)));
+    D.gm = m < 0 ? 0 : (m > kGuideN - 1 ? kGuideN - 1 : m);
+    D.tau = fmaxf(0.0f, nl.y);
+    // square roots v rsqrt(v) of the radius^2 and of 1 - mu^2 (0 for v <= 0)
+    const float rr = fmaxf(0.0f, nl.x);
+    const float mu = fmaf(2.0f, uc.x, -1.0f);
+    const float ss = fmaxf(0.0f, fmaf(-mu, mu, 1.0f));
+    const float2 rt = __fmul2_rn(make_float2(rr, ss), make_float2(rsqrtf(rr), rsqrtf(ss)));
+    D.rad = rr > 0.0f ? rt.x : 0.0f;
+    const float st = ss > 0.0f ? rt.y : 0.0f;
+    // sin and cos of 2 pi u through the shifted angle 2 pi (u - 1/2) in
+    // [-pi, pi] (negated back), for the phase and the azimuth
+    const float2 ang = __fmul2_rn(__fadd2_rn(make_float2(ub.x, uc.y), make_float2(-0.5f, -0.5f)),
+                                  make_float2(6.28318530717958648f, 6.28318530717958648f));
+    float sb, cb, sp, cp;
+    __sincosf(ang.x, &sb, &cb);
+    __sincosf(ang.y, &sp, &cp);
+    D.bc = -cb;
+    D.bs = -sb;
+    const float2 mxy = __fmul2_rn(make_float2(st, st), make_float2(-cp, -sp));
+    D.mx = mxy.x;
+    D.my = mxy.y;
+    D.mz = mu;
+    return D;
+}
+
 // ---------------------------------------------------------------- table lookups (shared memory)
 
 // H(a, x) from the ph_mode 2 slice: ln H linear in log10|x| between nodes;
@@ -285,8 +359,21 @@ __device__ __forceinline__ R us_sample(R x, R L, int m, const float* sx, const f
         if (ua) { ++ja; a0 = a1; a1 = (R)ra[ja + 1]; }
         if (ub) { ++jb; b0 = b1; b1 = (R)rb[jb + 1]; }
     }
-    const R ua_ = (R)kUsU0 + (R)kUsDu * (R)ja + (R)kUsDu * O::dv(L - a0, a1 - a0);
-    const R ub_ = (R)kUsU0 + (R)kUsDu * (R)jb + (R)kUsDu * O::dv(L - b0, b1 - b0);
+    R ua_, ub_;
+    if constexpr (sizeof(R) == 4) {
+        // both rows at once: u_j + du (L - c_j) / (c_j+1 - c_j)
+        const float2 num = sub2f(make_float2(L, L), make_float2(a0, b0));
+        const float2 den = sub2f(make_float2(a1, b1), make_float2(a0, b0));
+        const float2 fr = __fmul2_rn(num, make_float2(O::rcp(den.x), O::rcp(den.y)));
+        float2 u2 = __ffma2_rn(make_float2((float)kUsDu, (float)kUsDu), make_float2((float)ja, (float)jb),
+                               make_float2((float)kUsU0, (float)kUsU0));
+        u2 = __ffma2_rn(make_float2((float)kUsDu, (float)kUsDu), fr, u2);
+        ua_ = u2.x;
+        ub_ = u2.y;
+    } else {
+        ua_ = (R)kUsU0 + (R)kUsDu * (R)ja + (R)kUsDu * O::dv(L - a0, a1 - a0);
+        ub_ = (R)kUsU0 + (R)kUsDu * (R)jb + (R)kUsDu * O::dv(L - b0, b1 - b0);
+    }
     const R u = ((R)1 - t) * ua_ + t * ub_;
     return x < (R)0 ? -u : u;
 }
@@ -929,11 +1016,13 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
         // line-free cell gives an infinite or NaN distance: outside). The
         // face distances are needed only for a crossing.
         ds = O::dv(p.tau, alpha);
-        const float qx = fmaf(ds, p.nx, p.px), qy = fmaf(ds, p.ny, p.py), qz = fmaf(ds, p.nz, p.pz);
-        scat = fabsf(qx - 0.5f) <= 0.5f && fabsf(qy - 0.5f) <= 0.5f && fabsf(qz - 0.5f) <= 0.5f;
+        const float2 qxy = __ffma2_rn(make_float2(ds, ds), make_float2(p.nx, p.ny), make_float2(p.px, p.py));
+        const float qz = fmaf(ds, p.nz, p.pz);
+        const float2 hxy = __fadd2_rn(qxy, make_float2(-0.5f, -0.5f));
+        scat = fabsf(hxy.x) <= 0.5f && fabsf(hxy.y) <= 0.5f && fabsf(qz - 0.5f) <= 0.5f;
         if (scat) {
-            p.px = qx;
-            p.py = qy;
+            p.px = qxy.x;
+            p.py = qxy.y;
             p.pz = qz;
         } else {
             // a zero component counts as +1e-30 (the packet then crosses that
@@ -1010,15 +1099,31 @@ __device__ __forceinline__ bool advance(const TransportArgs& A, const RoundKeys&
         }
         // independent long-latency work first: Box-Muller, new direction,
         // the sampler's logs; then the table walk
-        R bs, bc;
-        O::sc2pi(O::uni(w0.w[2]), &bs, &bc);
-        const R rad = O::sq(fmax((R)0, -O::ln(O::uni(w0.w[1]))));
-        R mx, my, mz;
-        iso_dir<R>(O::uni(w1.w[0]), O::uni(w1.w[1]), mx, my, mz);
-        R L;
-        const int gm = us_bin<R>(O::uni(w0.w[0]), L);
-        const R tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
-        const R z1 = rad * bc, z2 = rad * bs;
+        R bs, bc, rad, mx, my, mz, L, tau_new, z1, z2;
+        int gm;
+        if constexpr (sizeof(R) == 4) {
+            const DrawsF D = draws_f32(w0, w1);
+            bs = D.bs;
+            bc = D.bc;
+            rad = D.rad;
+            mx = D.mx;
+            my = D.my;
+            mz = D.mz;
+            L = D.L;
+            gm = D.gm;
+            tau_new = D.tau;
+            const float2 z = __fmul2_rn(make_float2(rad, rad), make_float2(bc, bs));
+            z1 = z.x;
+            z2 = z.y;
+        } else {
+            O::sc2pi(O::uni(w0.w[2]), &bs, &bc);
+            rad = O::sq(fmax((R)0, -O::ln(O::uni(w0.w[1]))));
+            iso_dir<R>(O::uni(w1.w[0]), O::uni(w1.w[1]), mx, my, mz);
+            gm = us_bin<R>(O::uni(w0.w[0]), L);
+            tau_new = fmax((R)0, -O::ln(O::uni(w0.w[3])));
+            z1 = rad * bc;
+            z2 = rad * bs;
+        }
         const R us = us_sample<R>(xcom, L, gm, sx, sc, sg, rg);   // finite for any x; unused beyond 300
         const R upar = fabs(xcom) > (R)300 ? z2 : us;
         const R g = p.nx * mx + p.ny * my + p.nz * mz;
