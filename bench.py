@@ -452,7 +452,7 @@ def bench_next_rows(args, dev):
     # sphere at tau0 = 1e4 (2^19 packets: enough that the launch is not set
     # by its longest packets, as a short tau0 = 1e6 run would be)
     place = {}
-    for wl, q, npk in (("slab", base, 1_000_000), ("sphere64_tau1e4", W.sphere(tau0=1e4), 1 << 19)):
+    for wl, q, npk in (("slab", base, 200_000), ("sphere64_tau1e4", W.sphere(tau0=1e4), 1 << 19)):
         g = krl.Grid(q, device=dev)
         try:
             row = {}
@@ -465,7 +465,7 @@ def bench_next_rows(args, dev):
             place[wl] = row
         finally:
             g.close()
-    out["table_placement"] = {"workloads": "slab as above (1e6 packets); 64^3 tau0 = 1e4 sphere, 2^19 packets",
+    out["table_placement"] = {"workloads": "slab as above (2e5 packets); 64^3 tau0 = 1e4 sphere, 2^19 packets",
                               **place}
 
     # The paper's own timing setup (Sec. 3.5.2, Table 1: uniform 32^3 box,
