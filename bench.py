@@ -407,6 +407,7 @@ def bench_next_rows(args, dev):
     Sec. 3.2 dusty slab at (a tau0)^{1/3} tau_a = 1 (2e5 packets)."""
     import dataclasses
     import math
+    import numpy as np
     import torch
     import paper_2608_09340_gb300 as krl
     import workloads as W
@@ -431,10 +432,18 @@ def bench_next_rows(args, dev):
         n_iter, ppl = 20, 10_000_000          # the configuration's 20 cycles of 1e7 packets per line
         dt, ch = timed(lambda: g.levels_iterate(desc, n_iter, ppl, 2, pops, init_lte=True))
         n_lines = int((A > 0).sum())
+        # The largest change over the 2.1e6 cells settles, after the first
+        # cycle, at the Monte Carlo noise of the least-sampled cells; 4x the
+        # packets per line should halve that plateau (N^-1/2) if it is noise
+        _, ch4 = timed(lambda: g.levels_iterate(desc, 5, 4 * ppl, 3, pops, init_lte=True))
+        plateau = float(np.median(ch[1:]))
+        plateau4 = float(np.median(ch4[1:]))
         out["levels"] = {"workload": "cloud 128^3, 5-level rotor, 4 lines", "cycles": n_iter,
                          "packets_per_line": ppl, "s_per_cycle": dt / n_iter,
                          "packets_per_s": n_iter * n_lines * ppl / dt,
-                         "max_change": [float(c) for c in ch]}
+                         "max_change": [float(c) for c in ch],
+                         "plateau": plateau, "plateau_4x_packets": plateau4,
+                         "plateau_ratio": plateau / plateau4 if plateau4 > 0 else None}
     finally:
         g.close()
 

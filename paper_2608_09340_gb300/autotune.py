@@ -44,16 +44,24 @@ def _time(fn):
     return e0.elapsed_time(e1)
 
 
-def tune_batch(batch, packets, fraction: float = 0.2, space=None, seed: int = 12345):
+PILOT_SET_STRIDE = 1 << 40           # pilot set r starts at PILOT_FIRST_ID + r * stride
+
+
+def tune_batch(batch, packets, fraction: float = 0.2, space=None, seed: int = 12345, repeats: int = 2):
     """Best {block, refill_min, ctas_per_sm} for `batch` (a Batch) and the
-    per-model packet counts `packets`; returns (best, timings)."""
+    per-model packet counts `packets`; returns (best, timings). Each
+    candidate is timed on `repeats` disjoint pilot sets and ranked by the
+    sum: a pilot's time is set largely by its few longest packets, so one
+    set alone ranks close candidates by chance."""
     space = space or BATCH_SPACE
     pilot = [max(1, int(n * fraction)) for n in packets]
-    first = [PILOT_FIRST_ID] * len(pilot)
     timings = []
     for cand in _candidates(space):
         try:                            # a block the walk does not support raises: skip it
-            ms = _time(lambda: batch.run(pilot, first_ids=first, seed=seed, **cand))
+            ms = 0.0
+            for r in range(repeats):
+                first = [PILOT_FIRST_ID + r * PILOT_SET_STRIDE] * len(pilot)
+                ms += _time(lambda: batch.run(pilot, first_ids=first, seed=seed, **cand))
         except Exception:
             continue
         timings.append((ms, cand))

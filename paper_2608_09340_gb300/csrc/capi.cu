@@ -736,9 +736,20 @@ krl_status krl_raytrace_channels(krl_grid* g, const krl_raytrace_desc* d, float*
     A.v[0] = -sin(ph);
     A.v[1] = cos(ph);
     A.v[2] = 0.0;
+    // face ahead along -n on each axis: (1 - p) / d for d > 0, -p / d for
+    // d < 0, as one FMA; an axis the ray runs parallel to (or whose inverse
+    // overflows) gets a distance of 3e38, never the nearest
     for (int k = 0; k < 3; ++k) {
-        A.dirf[k] = (float)(-A.n[k]);
-        A.invf[k] = 1.0f / A.dirf[k];
+        const float d = (float)(-A.n[k]);
+        const float inv = 1.0f / d;
+        A.dirf[k] = d;
+        if (d != 0.0f && fabsf(inv) < 1e30f) {
+            A.face_neg[k] = -inv;
+            A.face_c[k] = d > 0.0f ? inv : 0.0f;
+        } else {
+            A.face_neg[k] = 0.0f;
+            A.face_c[k] = 3.0e38f;
+        }
     }
     A.centre[0] = 0.5 * g->nx;
     A.centre[1] = 0.5 * g->ny;

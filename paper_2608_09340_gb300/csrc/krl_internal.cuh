@@ -204,7 +204,9 @@ struct RayArgs {
     int n_ch;
     double ch_x0, ch_dx;      // v_min / b, dv / b
     double n[3], u[3], v[3];  // camera direction and image axes
-    float dirf[3], invf[3];   // the march direction -n in float and its reciprocal
+    float dirf[3];            // the march direction -n in float
+    float face_neg[3], face_c[3];   // distance to the face ahead on axis d from in-cell
+                                    // position p: fma(p, face_neg[d], face_c[d])
     double centre[3];         // image centre (box centre), cell units
     double pix;               // pixel size, cell units
     int npix_x, npix_y;

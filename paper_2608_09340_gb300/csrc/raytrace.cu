@@ -210,16 +210,6 @@ __global__ void __launch_bounds__(256) k_ray_setup(const RayArgs A)
     A.rayinit[2 * ray + 1] = make_float4(p[0], p[1], p[2], 0.0f);
 }
 
-// (1 - e^{-d})/d and e^{-d} without a branch: the exponential form above
-// d = 0.05, the series below.
-__device__ __forceinline__ float escape_factor_bf(float d)
-{
-    const float e = __expf(-d);
-    const float lg = __fdividef(1.0f - e, d);
-    const float sm = 1.0f - d * (0.5f - d * (1.0f / 6.0f - d * (1.0f / 24.0f - d * (1.0f / 120.0f))));
-    return d > 0.05f ? lg : sm;
-}
-
 // Two channels at a time with the paired FP32 instructions (sm_100 and
 // later; each half rounds as the single-precision operation would). a - b
 // is formed as fma(b, -1, a), exact in the product and rounded once.
@@ -263,14 +253,49 @@ __device__ __forceinline__ float2 escape_factor2(float2 d)
     return make_float2(d.x > 0.05f ? lg.x : sm.x, d.y > 0.05f ? lg.y : sm.y);
 }
 
+// One cell's extinction and emissivity for a lane's four channels, as two
+// pairs. FULL (n_ch = 4 LPR, rows 16-byte aligned): lane `sub` of a ray holds
+// channels 4 sub .. 4 sub + 3, read as one 16-byte vector per row, so a
+// ray's lanes read each row in one contiguous sweep. Otherwise pair h holds
+// channels sub + LPR (2h) and sub + LPR (2h + 1); channels past n_ch read zeros
+// (dtau = 0 and no intensity).
+template <int LPR, bool FULL>
+__device__ __forceinline__ void cell_rows(const RayArgs& A, int c, int sub, float2 (&v)[2], float2 (&j)[2])
+{
+    const float* arow = A.hcube + (size_t)c * A.n_ch;
+    const float* jrow = A.emiss + (size_t)c * A.n_ch;
+    if constexpr (FULL) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(arow) + sub);
+        const float4 e = __ldg(reinterpret_cast<const float4*>(jrow) + sub);
+        v[0] = make_float2(a.x, a.y);
+        v[1] = make_float2(a.z, a.w);
+        j[0] = make_float2(e.x, e.y);
+        j[1] = make_float2(e.z, e.w);
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ka = sub + LPR * (2 * h), kb = ka + LPR;
+            v[h] = make_float2(ka < A.n_ch ? __ldg(arow + ka) : 0.0f, kb < A.n_ch ? __ldg(arow + kb) : 0.0f);
+            j[h] = make_float2(ka < A.n_ch ? __ldg(jrow + ka) : 0.0f, kb < A.n_ch ? __ldg(jrow + kb) : 0.0f);
+        }
+    }
+}
+
+// Channel of element e of pair h of lane `sub` (the layout of cell_rows).
+template <int LPR, bool FULL>
+__device__ __forceinline__ int lane_channel(int sub, int h, int e)
+{
+    return FULL ? 4 * sub + 2 * h + e : sub + LPR * (2 * h + e);
+}
+
 // The trace over the per-camera cube (k_rt_profile): LPR lanes per ray, 4
-// channels per lane (lane l of a ray holds channels l + LPR q, q < 4), so a
-// warp follows 32 / LPR neighbouring rays, whose walks through the grid
-// nearly coincide. The per-segment work (face distances, cell index) is
-// shared by fewer lanes' worth of channels than with one ray per warp. The
-// cube holds the extinction alpha0 H + alpha_abs (JL false) or H (JL true:
-// the line-emission term needs H; alpha is formed here).
-template <int LPR, bool JL>
+// channels per lane, so a warp follows 32 / LPR neighbouring rays, whose
+// walks through the grid nearly coincide. The per-segment work (face
+// distances, cell index) is shared by fewer lanes' worth of channels than
+// with one ray per warp. The cube holds the extinction alpha0 H + alpha_abs
+// (JL false) or H (JL true: the line-emission term needs H; alpha is formed
+// here).
+template <int LPR, bool JL, bool FULL>
 __global__ void __launch_bounds__(256, 5) k_trace_cube(const RayArgs A)
 {
     constexpr int CPL = 4;
@@ -284,31 +309,36 @@ __global__ void __launch_bounds__(256, 5) k_trace_cube(const RayArgs A)
 
     // the ray's start (k_ray_setup): first cell, position in it, hit
     const float4 r0 = __ldg(A.rayinit + 2 * ray), r1 = __ldg(A.rayinit + 2 * ray + 1);
-    // channels (2h, 2h + 1) of this lane in pair h: intensity, optical depth
-    // in front of the segment, and their compensation terms
+    // the lane's channel pairs: intensity, optical depth in front of the
+    // segment, and their compensation terms
     float2 I[CPL / 2], Ic[CPL / 2], tau[CPL / 2], tc[CPL / 2];
 #pragma unroll
     for (int h = 0; h < CPL / 2; ++h) I[h] = Ic[h] = tau[h] = tc[h] = make_float2(0.0f, 0.0f);
 
     if (__float_as_int(r0.w)) {
         int ci[3] = {__float_as_int(r0.x), __float_as_int(r0.y), __float_as_int(r0.z)};
-        float p[3] = {r1.x, r1.y, r1.z}, dir[3], inv[3];
+        float p[3] = {r1.x, r1.y, r1.z}, dir[3], fneg[3], fc[3];
         for (int d = 0; d < 3; ++d) {        // (from the parameter block: no FP64 per ray)
             dir[d] = A.dirf[d];
-            inv[d] = A.invf[d];
+            fneg[d] = A.face_neg[d];
+            fc[d] = A.face_c[d];
         }
-        const int max_seg = A.nx + A.ny + A.nz + 3;
+        // the ray's start can lie outside (a ray along the box's face); after
+        // that only the axis just stepped on can leave the box
+        const bool inside = ci[0] >= 0 && ci[0] < A.nx && ci[1] >= 0 && ci[1] < A.ny && ci[2] >= 0 && ci[2] < A.nz;
+        const unsigned fwd = (dir[0] > 0.0f ? 1u : 0u) | (dir[1] > 0.0f ? 2u : 0u) | (dir[2] > 0.0f ? 4u : 0u);
+        const int max_seg = inside ? A.nx + A.ny + A.nz + 3 : 0;
         for (int seg = 0; seg < max_seg; ++seg) {
-            if (ci[0] < 0 || ci[0] >= A.nx || ci[1] < 0 || ci[1] >= A.ny || ci[2] < 0 || ci[2] >= A.nz) break;
-            float s = 3.0e38f;
+            // distance to the face ahead on each axis, one FMA each
+            float s = fmaf(p[0], fneg[0], fc[0]);
             int axis = 0;
-            for (int d = 0; d < 3; ++d) {
-                float t = dir[d] > 0.0f ? (1.0f - p[d]) * inv[d] : (dir[d] < 0.0f ? -p[d] * inv[d] : 3.0e38f);
+            for (int d = 1; d < 3; ++d) {
+                const float t = fmaf(p[d], fneg[d], fc[d]);
                 if (t < s) { s = t; axis = d; }
             }
             const int c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
-            const float* arow = A.hcube + (size_t)c * A.n_ch;
-            const float* jrow = A.emiss + (size_t)c * A.n_ch;
+            float2 v[2], j[2];
+            cell_rows<LPR, FULL>(A, c, sub, v, j);
             float a0 = 0.0f, ta = 0.0f, jl = 0.0f;
             if (JL) {
                 a0 = __ldg(A.cells + c).x;
@@ -318,29 +348,29 @@ __global__ void __launch_bounds__(256, 5) k_trace_cube(const RayArgs A)
             const float2 s2 = make_float2(s, s);
 #pragma unroll
             for (int h = 0; h < CPL / 2; ++h) {
-                // channels past n_ch read zeros: dtau = 0 and no intensity
-                const int ka = sub + LPR * (2 * h), kb = ka + LPR;
-                float2 v = make_float2(ka < A.n_ch ? __ldg(arow + ka) : 0.0f, kb < A.n_ch ? __ldg(arow + kb) : 0.0f);
-                float2 j = make_float2(ka < A.n_ch ? __ldg(jrow + ka) : 0.0f, kb < A.n_ch ? __ldg(jrow + kb) : 0.0f);
+                float2 vv = v[h], jj = j[h];
                 if (JL) {
-                    j = __ffma2_rn(make_float2(jl, jl), v, j);
-                    v = __ffma2_rn(make_float2(a0, a0), v, make_float2(ta, ta));
+                    jj = __ffma2_rn(make_float2(jl, jl), vv, jj);
+                    vv = __ffma2_rn(make_float2(a0, a0), vv, make_float2(ta, ta));
                 }
-                const float2 dtau = __fmul2_rn(v, s2);
+                const float2 dtau = __fmul2_rn(vv, s2);
                 const float2 T = exp_neg2(tau[h]);
-                kahan_add2(I[h], Ic[h], __fmul2_rn(__fmul2_rn(__fmul2_rn(T, j), s2), escape_factor2(dtau)));
+                kahan_add2(I[h], Ic[h], __fmul2_rn(__fmul2_rn(__fmul2_rn(T, jj), s2), escape_factor2(dtau)));
                 kahan_add2(tau[h], tc[h], dtau);
             }
-            for (int d = 0; d < 3; ++d)
-                if (d != axis) p[d] = fminf(1.0f, fmaxf(0.0f, fmaf(s, dir[d], p[d])));
-            const int step = dir[axis] > 0.0f ? 1 : -1;
-            ci[axis] += step;
-            p[axis] = step > 0 ? 0.0f : 1.0f;
+            // move to the face (the crossing axis is then set exactly)
+            for (int d = 0; d < 3; ++d) p[d] = __saturatef(fmaf(s, dir[d], p[d]));
+            const bool up = (fwd >> axis) & 1u;
+            const int nc = ci[axis] + (up ? 1 : -1);
+            const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
+            if ((unsigned)nc >= (unsigned)dim) break;
+            ci[axis] = nc;
+            p[axis] = up ? 0.0f : 1.0f;
         }
     }
 #pragma unroll
     for (int h = 0; h < CPL / 2; ++h) {
-        const int ka = sub + LPR * (2 * h), kb = ka + LPR;
+        const int ka = lane_channel<LPR, FULL>(sub, h, 0), kb = lane_channel<LPR, FULL>(sub, h, 1);
         if (ka < A.n_ch) A.maps[((size_t)ka * A.npix_y + iy) * A.npix_x + ix] = I[h].x;
         if (kb < A.n_ch) A.maps[((size_t)kb * A.npix_y + iy) * A.npix_x + ix] = I[h].y;
     }
@@ -481,12 +511,17 @@ cudaError_t launch_cpl(const RayArgs& A, int sm_count, cudaStream_t s)
         const long long blocks = (npix * LPR + 255) / 256;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         k_ray_setup<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(A);
+        // the vector reads need each lane's four channels 16-byte aligned
+        const bool full = A.n_ch == 4 * LPR && (reinterpret_cast<uintptr_t>(A.emiss) & 15u) == 0 &&
+                          (reinterpret_cast<uintptr_t>(A.hcube) & 15u) == 0;
         if (A.jline) {
             k_rt_profile<CPL, false><<<sm_count * 8, 256, 0, s>>>(A, A.hcube);
-            k_trace_cube<LPR, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+            if (full) k_trace_cube<LPR, true, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+            else k_trace_cube<LPR, true, false><<<(unsigned)blocks, 256, 0, s>>>(A);
         } else {
             k_rt_profile<CPL, true><<<sm_count * 8, 256, 0, s>>>(A, A.hcube);
-            k_trace_cube<LPR, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+            if (full) k_trace_cube<LPR, false, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+            else k_trace_cube<LPR, false, false><<<(unsigned)blocks, 256, 0, s>>>(A);
         }
     } else {
         const long long blocks = (npix * 32 + 255) / 256;

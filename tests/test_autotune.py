@@ -65,8 +65,12 @@ def test_tune_batch(monkeypatch):
     monkeypatch.setattr(AT, "_time", fake_time)
     best, timings = AT.tune_batch(b, [1000, 10, 3], fraction=0.2)
     assert best == {"block": 256, "refill_min": 4, "ctas_per_sm": 0}
-    assert len(timings) == 12
-    for packets, first, seed, _ in b.calls:
+    assert len(timings) == 12 and len(b.calls) == 24   # each candidate on two pilot sets
+    for i, (packets, first, seed, _) in enumerate(b.calls):
         assert packets == [200, 2, 1]               # at least one pilot packet per model
-        assert first == [AT.PILOT_FIRST_ID] * 3
+        assert first == [AT.PILOT_FIRST_ID + (i % 2) * AT.PILOT_SET_STRIDE] * 3
+    # the two sets are disjoint id ranges, far above the real runs' ids
+    assert AT.PILOT_SET_STRIDE > 1000 and AT.PILOT_FIRST_ID + 2 * AT.PILOT_SET_STRIDE < 1 << 64
+    assert [t[0] for t in timings] == sorted(t[0] for t in timings)
+    assert timings[0][0] == 2 * _cost(best)
     assert all(g.resets == 1 for g in b.grids)

@@ -76,16 +76,23 @@ def test_thin_slab_two_step_chain():
     assert np.max(np.abs(img / img.sum() - shape / shape.sum())) / np.max(shape / shape.sum()) < 0.02
 
 
-@pytest.mark.parametrize("n_ch", [3, 8, 20, 33, 64, 100])
-def test_channel_counts_and_lane_groups(n_ch):
+@pytest.mark.parametrize("n_ch,offset", [(3, 0), (8, 0), (20, 0), (33, 0), (64, 0), (64, 1), (100, 0), (128, 0)])
+def test_channel_counts_and_lane_groups(n_ch, offset):
     """Every lanes-per-ray variant of the trace (1 .. 32 lanes, 4 channels
-    each; ragged channel counts) and the per-segment fallback, on a random
-    emissivity through a moving envelope, against the FP64 trace."""
+    each; ragged channel counts, and channel counts that fill every lane,
+    read as one 16-byte vector per lane) and the per-segment fallback, on a
+    random emissivity through a moving envelope, against the FP64 trace.
+    offset = 1: the emissivity starts 4 bytes past a 16-byte boundary, so a
+    full channel count takes the unvectorised reads."""
     krl = need_gpu()
     import torch
     p = W.envelope(n=12, n_ch=n_ch, n_packets=1)
     rng = np.random.default_rng(n_ch)
-    em = torch.from_numpy(rng.random((p.ncell, n_ch), dtype=np.float32)).cuda()
+    em_host = rng.random((p.ncell, n_ch), dtype=np.float32)
+    buf = torch.zeros(p.ncell * n_ch + 4, dtype=torch.float32, device="cuda")
+    em = buf[offset:offset + p.ncell * n_ch].view(p.ncell, n_ch)
+    em.copy_(torch.from_numpy(em_host))
+    assert (em.data_ptr() % 16 == 0) == (offset == 0)
     th, ph = math.radians(40.0), math.radians(25.0)
     q = W.envelope(n=12, n_ch=n_ch, n_packets=1)
     q.cameras = ((th, ph),)
