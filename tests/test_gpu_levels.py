@@ -7,7 +7,7 @@ import pytest
 import oracle
 import workloads as W
 from oracle import levels as LV
-from _gpu_common import need_gpu
+from _gpu_common import need_gpu, report
 
 pytestmark = pytest.mark.gpu
 
@@ -85,3 +85,30 @@ def test_lambda_iteration_matches_oracle():
     # the iteration moves the populations away from LTE toward subthermal excitation
     lte = LV.boltzmann(lev, p.T_K, n_mol.reshape(-1))
     assert np.mean(got[:, 0] > lte[:, 0]) > 0.9
+
+
+def test_lambda_iteration_settles_at_the_sampling_floor():
+    """Sec. 2.1.3 runs the Lambda iteration to convergence without a stated
+    criterion. After the first cycle the largest population change over the
+    cells, max |dn| / n_mol, stops falling: what is left is the Monte Carlo
+    noise of the radiative rates, so 4x the packets per line roughly halves
+    that floor (N^-1/2), and the floor shows no trend over the cycles."""
+    krl = need_gpu()
+    import torch
+    p, n_mol, spec = W.cloud(n=16, seed=11, packets_per_line=200_000)
+    lev = LV.rotor(spec.n_lev, spec.B_K, spec.A1, spec.k_ul, spec.mass_amu)
+    g = krl.Grid(p)
+    try:
+        nm_t = torch.from_numpy(n_mol.reshape(-1)).cuda()
+        pops = torch.zeros((p.ncell, lev.n), dtype=torch.float64, device="cuda")
+        ch1 = np.asarray(g.levels_iterate(_desc(krl, lev, nm_t), 8, 200_000, 5, pops, init_lte=True))
+        ch4 = np.asarray(g.levels_iterate(_desc(krl, lev, nm_t), 5, 800_000, 6, pops, init_lte=True))
+    finally:
+        g.close()
+    floor1, floor4 = np.median(ch1[1:]), np.median(ch4[1:])
+    report("lambda_floor_16cube", floor_2e5=floor1, floor_8e5=floor4, ratio=floor1 / floor4,
+           first_change=float(ch1[0]), changes=[float(c) for c in ch1])
+    assert ch1[0] > 1.5 * floor1                        # the first cycle leaves LTE
+    assert 1.3 < floor1 / floor4 < 3.0, (floor1, floor4)
+    # no drift: the later cycles' floor matches the earlier cycles'
+    assert abs(np.median(ch1[1:4]) - np.median(ch1[4:])) < 0.35 * floor1, ch1
