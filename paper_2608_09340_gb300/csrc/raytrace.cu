@@ -296,7 +296,7 @@ __device__ __forceinline__ int lane_channel(int sub, int h, int e)
 // (JL false) or H (JL true: the line-emission term needs H; alpha is formed
 // here).
 template <int LPR, bool JL, bool FULL>
-__global__ void __launch_bounds__(256, 5) k_trace_cube(const RayArgs A)
+__global__ void __launch_bounds__(256, 4) k_trace_cube(const RayArgs A)
 {
     constexpr int CPL = 4;
     const int lane = threadIdx.x & 31;
@@ -316,27 +316,27 @@ __global__ void __launch_bounds__(256, 5) k_trace_cube(const RayArgs A)
     for (int h = 0; h < CPL / 2; ++h) I[h] = Ic[h] = tau[h] = tc[h] = make_float2(0.0f, 0.0f);
 
     if (__float_as_int(r0.w)) {
-        int ci[3] = {__float_as_int(r0.x), __float_as_int(r0.y), __float_as_int(r0.z)};
-        float p[3] = {r1.x, r1.y, r1.z}, dir[3], fneg[3], fc[3];
-        for (int d = 0; d < 3; ++d) {        // (from the parameter block: no FP64 per ray)
-            dir[d] = A.dirf[d];
-            fneg[d] = A.face_neg[d];
-            fc[d] = A.face_c[d];
-        }
+        // cell and in-cell position as scalars (an array indexed by the
+        // crossing axis would live in local memory); the crossing axis is
+        // applied by selects
+        int ci0 = __float_as_int(r0.x), ci1 = __float_as_int(r0.y), ci2 = __float_as_int(r0.z);
+        float p0 = r1.x, p1 = r1.y, p2 = r1.z;
+        const float d0 = A.dirf[0], d1 = A.dirf[1], d2 = A.dirf[2];
+        const int nx = A.nx, ny = A.ny, nz = A.nz, nxy = A.nx * A.ny;
         // the ray's start can lie outside (a ray along the box's face); after
         // that only the axis just stepped on can leave the box
-        const bool inside = ci[0] >= 0 && ci[0] < A.nx && ci[1] >= 0 && ci[1] < A.ny && ci[2] >= 0 && ci[2] < A.nz;
-        const unsigned fwd = (dir[0] > 0.0f ? 1u : 0u) | (dir[1] > 0.0f ? 2u : 0u) | (dir[2] > 0.0f ? 4u : 0u);
-        const int max_seg = inside ? A.nx + A.ny + A.nz + 3 : 0;
+        const bool inside = ci0 >= 0 && ci0 < nx && ci1 >= 0 && ci1 < ny && ci2 >= 0 && ci2 < nz;
+        const unsigned fwd = (d0 > 0.0f ? 1u : 0u) | (d1 > 0.0f ? 2u : 0u) | (d2 > 0.0f ? 4u : 0u);
+        const int max_seg = inside ? nx + ny + nz + 3 : 0;
+        int c = (ci2 * ny + ci1) * nx + ci0;
         for (int seg = 0; seg < max_seg; ++seg) {
             // distance to the face ahead on each axis, one FMA each
-            float s = fmaf(p[0], fneg[0], fc[0]);
+            float s = fmaf(p0, A.face_neg[0], A.face_c[0]);
             int axis = 0;
-            for (int d = 1; d < 3; ++d) {
-                const float t = fmaf(p[d], fneg[d], fc[d]);
-                if (t < s) { s = t; axis = d; }
-            }
-            const int c = (ci[2] * A.ny + ci[1]) * A.nx + ci[0];
+            const float t1 = fmaf(p1, A.face_neg[1], A.face_c[1]);
+            if (t1 < s) { s = t1; axis = 1; }
+            const float t2 = fmaf(p2, A.face_neg[2], A.face_c[2]);
+            if (t2 < s) { s = t2; axis = 2; }
             float2 v[2], j[2];
             cell_rows<LPR, FULL>(A, c, sub, v, j);
             float a0 = 0.0f, ta = 0.0f, jl = 0.0f;
@@ -358,14 +358,24 @@ __global__ void __launch_bounds__(256, 5) k_trace_cube(const RayArgs A)
                 kahan_add2(I[h], Ic[h], __fmul2_rn(__fmul2_rn(__fmul2_rn(T, jj), s2), escape_factor2(dtau)));
                 kahan_add2(tau[h], tc[h], dtau);
             }
-            // move to the face (the crossing axis is then set exactly)
-            for (int d = 0; d < 3; ++d) p[d] = __saturatef(fmaf(s, dir[d], p[d]));
+            // move to the face, then step across it (the crossing axis is set exactly)
+            p0 = __saturatef(fmaf(s, d0, p0));
+            p1 = __saturatef(fmaf(s, d1, p1));
+            p2 = __saturatef(fmaf(s, d2, p2));
+            const bool x0 = axis == 0, x1 = axis == 1;
             const bool up = (fwd >> axis) & 1u;
-            const int nc = ci[axis] + (up ? 1 : -1);
-            const int dim = axis == 0 ? A.nx : (axis == 1 ? A.ny : A.nz);
+            const int nc = (x0 ? ci0 : (x1 ? ci1 : ci2)) + (up ? 1 : -1);
+            const int dim = x0 ? nx : (x1 ? ny : nz);
             if ((unsigned)nc >= (unsigned)dim) break;
-            ci[axis] = nc;
-            p[axis] = up ? 0.0f : 1.0f;
+            const float pn = up ? 0.0f : 1.0f;
+            ci0 = x0 ? nc : ci0;
+            ci1 = x1 ? nc : ci1;
+            ci2 = (x0 || x1) ? ci2 : nc;
+            p0 = x0 ? pn : p0;
+            p1 = x1 ? pn : p1;
+            p2 = (x0 || x1) ? p2 : pn;
+            const int stride = x0 ? 1 : (x1 ? nx : nxy);
+            c += up ? stride : -stride;
         }
     }
 #pragma unroll
