@@ -144,19 +144,34 @@ __global__ void __launch_bounds__(256) k_rt_profile(const RayArgs A, float* hc)
     }
     const float a = A.a;
     const float H0 = __ldg(A.H0);
+    // a warp takes 32 consecutive cells: each lane forms one cell's n.V (and
+    // reads its record), then the warp fills the cells' channel rows one
+    // after the other with those values broadcast
+    const long long ngroups = (ncell + 31) / 32;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncell; c += nwarps) {
-        const float4 rec = __ldg(A.cells + c);
-        const float ta = (ALPHA && A.tau_abs) ? __ldg(A.tau_abs + c) : 0.0f;
-        float vnh, vnl;
-        dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
+    for (long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; grp < ngroups; grp += nwarps) {
+        const long long c0 = grp * 32;
+        const long long cl = c0 + lane;
+        float vnh = 0.0f, vnl = 0.0f, a0 = 0.0f, ta = 0.0f;
+        if (cl < ncell) {
+            const float4 rec = __ldg(A.cells + cl);
+            a0 = rec.x;
+            if (ALPHA && A.tau_abs) ta = __ldg(A.tau_abs + cl);
+            dot_ff(nh, nl, rec.y, rec.z, rec.w, vnh, vnl);
+        }
+        const int cells = ncell - c0 < 32 ? (int)(ncell - c0) : 32;
+        for (int i = 0; i < cells; ++i) {
+            const float h = __shfl_sync(0xffffffffu, vnh, i), l = __shfl_sync(0xffffffffu, vnl, i);
+            const float ca = __shfl_sync(0xffffffffu, a0, i), ct = __shfl_sync(0xffffffffu, ta, i);
+            float* row = hc + (size_t)(c0 + i) * A.n_ch;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-            const int k = lane + 32 * q;
-            if (k < A.n_ch) {
-                const float xk = (xbh[q] - vnh) + (xbl[q] - vnl);
-                const float H = voigt_rt(xk, sv, eI, eF, a, H0);
-                hc[(size_t)c * A.n_ch + k] = ALPHA ? fmaf(rec.x, H, ta) : H;
+            for (int q = 0; q < CPL; ++q) {
+                const int k = lane + 32 * q;
+                if (k < A.n_ch) {
+                    const float xk = (xbh[q] - h) + (xbl[q] - l);
+                    const float H = voigt_rt(xk, sv, eI, eF, a, H0);
+                    row[k] = ALPHA ? fmaf(ca, H, ct) : H;
+                }
             }
         }
     }
