@@ -365,7 +365,14 @@ def bench_batch(args, dev, tau_range=None, total_packets=None, with_graph=True, 
 
     try:
         b = krl.Batch(grids)
-        best = tuned if tuned is not None else autotune.tune_batch(b, pk)[0]
+        # pilots of the full size (disjoint ids): a smaller pilot's time is set
+        # by its own few longest packets and ranked close candidates by chance
+        tune_table = None
+        if tuned is not None:
+            best = tuned
+        else:
+            best, timings = autotune.tune_batch(b, pk, fraction=1.0, repeats=1)
+            tune_table = [[round(ms / 1e3, 4), cand] for ms, cand in timings]
         b.run(pk, seed=7, **best)                                  # warm-up
         for g in grids:
             g.reset()
@@ -391,7 +398,7 @@ def bench_batch(args, dev, tau_range=None, total_packets=None, with_graph=True, 
         for g in grids:
             g.close()
     return {"workload": f"{BATCH_MODELS} spheres, tau0 log-U{list(tau_range)}, {total_packets} packets",
-            "scatterings": scat, "tuned": best,
+            "scatterings": scat, "tuned": best, "tuning_s_per_candidate": tune_table,
             "batched_scat_per_s": scat / t_batch, "graph_scat_per_s": scat / t_graph if t_graph else None,
             "per_model_scat_per_s": scat / t_single, "speedup_vs_per_model": t_single / t_batch,
             "s_batched": t_batch, "s_graph": t_graph, "s_per_model": t_single}
