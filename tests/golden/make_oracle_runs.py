@@ -45,6 +45,8 @@ CASES = {
     # the 64^3, tau0 = 1e6 sphere (static; outflow and infall at 200 km/s)
     "sphere64_tau1e6_static_n2e4_seed0": ("sphere", {}, 0, 20_000, 0, 20),
     "sphere64_tau1e6_static_n2e4_seed1": ("sphere", {}, 0, 20_000, 1, 20),
+    # the static sphere at 2e5 packets (two-sample L1 floor ~2.3 %)
+    "sphere64_tau1e6_static_n2e5_seed2": ("sphere", {}, 0, 200_000, 2, 20),
     "sphere64_tau1e6_out200_n2e5_seed0": ("sphere", {"vmax_kms": 200.0}, 0, 200_000, 0, 20),
     "sphere64_tau1e6_in200_n2e5_seed0": ("sphere", {"vmax_kms": -200.0}, 0, 200_000, 0, 20),
     # the 32^3, tau0 = 1e5 moving spheres, at the size where their spectra's

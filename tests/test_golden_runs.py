@@ -76,6 +76,22 @@ def test_sphere_runs_against_the_physics():
     assert chi2_two_sample(out, inn[::-1])[2] > 1e-3
 
 
+def test_static_sphere_at_2e5_packets():
+    """The 2e5-packet static headline run (third seed): its peak sits at the
+    sphere's 0.931 (a tau0)^{1/3} within 5 % (the 2e4-packet runs allow 15 %),
+    its spectrum is symmetric, and it agrees with the independent 2e4-packet
+    run of seed 0 (two-sample chi^2)."""
+    from _gpu_common import chi2_two_sample
+    big = S.load("sphere64_tau1e6_static_n2e5_seed2")
+    c = np.asarray(big["spec_c"][1:-1], dtype=np.float64)
+    pred = 0.931 * (4.7e-4 * 1e6) ** (1.0 / 3.0)
+    assert abs(x_peak(c, -60.0, 60.0, pred) / pred - 1.0) < 0.05
+    assert chi2_two_sample(c[:200][::-1], c[200:])[2] > 1e-3
+    small = S.load("sphere64_tau1e6_static_n2e4_seed0")
+    assert chi2_two_sample(np.asarray(small["spec_c"]), np.asarray(big["spec_c"]))[2] > 1e-3
+    assert abs(big["nscat_sum"] / big["n"] / (small["nscat_sum"] / small["n"]) - 1.0) < 0.03
+
+
 def test_two_seed_floors_match_their_expectation():
     """The measured two-seed L1 distance of each pair of stored runs sits at
     its expected value 2 sqrt(B_eff / (pi N)) (within 25 %): the stored
