@@ -49,6 +49,9 @@ CASES = {
     "sphere64_tau1e6_static_n2e5_seed2": ("sphere", {}, 0, 200_000, 2, 20),
     "sphere64_tau1e6_out200_n2e5_seed0": ("sphere", {"vmax_kms": 200.0}, 0, 200_000, 0, 20),
     "sphere64_tau1e6_in200_n2e5_seed0": ("sphere", {"vmax_kms": -200.0}, 0, 200_000, 0, 20),
+    # second seeds of the moving headline spheres, for their measured two-seed floors
+    "sphere64_tau1e6_out200_n2e5_seed1": ("sphere", {"vmax_kms": 200.0}, 0, 200_000, 1, 20),
+    "sphere64_tau1e6_in200_n2e5_seed1": ("sphere", {"vmax_kms": -200.0}, 0, 200_000, 1, 20),
     # the 32^3, tau0 = 1e5 moving spheres, at the size where their spectra's
     # two-sample floor is below 1 %; two seeds each for the measured floor
     "sphere32_tau1e5_out200_n6e5_seed0": ("sphere", {"vmax_kms": 200.0, "tau0": 1e5, "n": 32}, 0, 600_000, 0, 20),

@@ -98,6 +98,8 @@ def test_two_seed_floors_match_their_expectation():
     runs are independent samples of one distribution."""
     from _gpu_common import rel_l1
     for a, b in [("sphere64_tau1e6_static_n2e4_seed0", "sphere64_tau1e6_static_n2e4_seed1"),
+                 ("sphere64_tau1e6_out200_n2e5_seed0", "sphere64_tau1e6_out200_n2e5_seed1"),
+                 ("sphere64_tau1e6_in200_n2e5_seed0", "sphere64_tau1e6_in200_n2e5_seed1"),
                  ("sphere32_tau1e5_out200_n6e5_seed0", "sphere32_tau1e5_out200_n6e5_seed1"),
                  ("sphere32_tau1e5_in200_n6e5_seed0", "sphere32_tau1e5_in200_n6e5_seed1")]:
         ra, rb = S.load(a), S.load(b)
@@ -113,6 +115,8 @@ def test_two_seed_shell_z_is_moderate():
     (independent samples of one distribution) stay within the gate the GPU
     comparisons use (|z| < 4.5), with the sparse outer shells merged."""
     for a, b in [("sphere64_tau1e6_static_n2e4_seed0", "sphere64_tau1e6_static_n2e4_seed1"),
+                 ("sphere64_tau1e6_out200_n2e5_seed0", "sphere64_tau1e6_out200_n2e5_seed1"),
+                 ("sphere64_tau1e6_in200_n2e5_seed0", "sphere64_tau1e6_in200_n2e5_seed1"),
                  ("sphere32_tau1e5_out200_n6e5_seed0", "sphere32_tau1e5_out200_n6e5_seed1"),
                  ("sphere32_tau1e5_in200_n6e5_seed0", "sphere32_tau1e5_in200_n6e5_seed1")]:
         ra, rb = S.load(a), S.load(b)
