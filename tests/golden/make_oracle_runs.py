@@ -42,6 +42,7 @@ CASES = {
     # the static slab of the Neufeld test at the size where the two-sample
     # L1 noise floor of its 200-bin spectrum is below 1 %
     "slab64_tau1e4_n1e6_seed0": ("slab", {}, 0, 1_000_000, 0, 1),
+    "slab64_tau1e4_n1e6_seed1": ("slab", {}, 0, 1_000_000, 1, 1),
     # the 64^3, tau0 = 1e6 sphere (static; outflow and infall at 200 km/s)
     "sphere64_tau1e6_static_n2e4_seed0": ("sphere", {}, 0, 20_000, 0, 20),
     "sphere64_tau1e6_static_n2e4_seed1": ("sphere", {}, 0, 20_000, 1, 20),

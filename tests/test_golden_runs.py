@@ -98,6 +98,7 @@ def test_two_seed_floors_match_their_expectation():
     runs are independent samples of one distribution."""
     from _gpu_common import rel_l1
     for a, b in [("sphere64_tau1e6_static_n2e4_seed0", "sphere64_tau1e6_static_n2e4_seed1"),
+                 ("slab64_tau1e4_n1e6_seed0", "slab64_tau1e4_n1e6_seed1"),
                  ("sphere64_tau1e6_out200_n2e5_seed0", "sphere64_tau1e6_out200_n2e5_seed1"),
                  ("sphere64_tau1e6_in200_n2e5_seed0", "sphere64_tau1e6_in200_n2e5_seed1"),
                  ("sphere32_tau1e5_out200_n6e5_seed0", "sphere32_tau1e5_out200_n6e5_seed1"),
